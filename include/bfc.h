@@ -1,0 +1,173 @@
+/*
+ * bfc.h -- exact and sampled butterfly counting in bipartite graphs on one
+ * GB300 (sm_103a).  C ABI: plain pointers and sizes, no C++ or framework types.
+ *
+ * Method: Sanei-Mehri, Sariyuce, Tirthapura, "Butterfly Counting in Bipartite
+ * Networks" (arXiv 1801.00338).
+ *
+ * Graph model (Section 2): a simple bipartite graph G = (L u R, E), E a subset
+ * of L x R.  This library calls L "U" (ids 0..nU-1) and R "V" (ids 0..nV-1);
+ * an edge is a pair (u, v).  A butterfly is a 2x2 biclique {a, b} x {x, y};
+ * B is their number, b_v the number that contain vertex v, b_e the number that
+ * contain edge e.
+ *
+ * Canonical edge order: edge ids 0..m-1 number the DISTINCT edges in
+ * lexicographic (u, v) order.  Per-edge outputs use this order.
+ *
+ * Conventions for every call:
+ *   - Return value: BFC_OK (0) or a negative BFC_E* code; bfc_strerror() names it.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Work is enqueued on it in order.
+ *   - Host scalar outputs (uint64_t*, double* documented as host) are written
+ *     before the call returns; the call synchronises `stream` for them.
+ *   - Device array outputs are caller-owned device memory, written in stream
+ *     order; the caller synchronises before reading them.
+ *   - The library owns only bfc_graph and bfc_proposal handles and the device
+ *     memory they hold; inputs are borrowed for the duration of the call.
+ *   - All counts are exact unsigned 64-bit integers.
+ *   - A handle may be used by one stream at a time.
+ */
+#ifndef BFC_H
+#define BFC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define BFC_OK          0
+#define BFC_EINVAL     -1   /* null pointer, bad flag, bad size or parameter   */
+#define BFC_ERANGE     -2   /* a vertex id >= nU or >= nV, or m >= 2^32         */
+#define BFC_EDUP       -3   /* duplicate edge and BFC_DEDUP not set             */
+#define BFC_ENOMEM     -4   /* device or host allocation failed                 */
+#define BFC_ECUDA      -5   /* a CUDA runtime call failed                       */
+#define BFC_ETIMEOUT   -6   /* a device wait hit its iteration limit            */
+#define BFC_EOVERFLOW  -7   /* a count exceeded its integer range               */
+#define BFC_EINTERNAL  -8   /* a device-side consistency check failed           */
+
+/* ---- flags ------------------------------------------------------------ */
+/* bfc_graph_from_edges */
+#define BFC_INPUT_DEVICE  0x1u  /* u, v are device pointers (else host)        */
+#define BFC_DEDUP         0x2u  /* drop repeated edges instead of BFC_EDUP      */
+/* counting calls: which side holds the start vertices (Algorithm 1).
+ * AUTO follows Algorithm 1: start from L (= U) unless
+ * sum_{L} d^2 < sum_{R} d^2, then from R. */
+#define BFC_SIDE_AUTO     0x0u
+#define BFC_SIDE_U        0x10u
+#define BFC_SIDE_V        0x20u
+
+typedef struct bfc_graph bfc_graph;
+typedef struct bfc_proposal bfc_proposal;
+
+/* ---- graph ------------------------------------------------------------- */
+
+/* Build a graph from an edge list (Section 2: simple bipartite graph; input
+ * cleaning as in "Networks and Experimental Setup").
+ *   u[i], v[i]  : endpoints of edge i, u in [0, nU), v in [0, nV); host or
+ *                 device memory per BFC_INPUT_DEVICE; length m (m < 2^32).
+ *   flags       : BFC_INPUT_DEVICE | BFC_DEDUP.
+ *   out         : receives the handle (free with bfc_graph_free).
+ * The handle keeps both adjacency structures (rows of U and rows of V, each
+ * sorted) on the device.  Vertices of degree 0 are kept: they count in n for
+ * vertex sampling and get b_v = 0.
+ * Errors: BFC_EINVAL (null pointers, nU or nV == 0), BFC_ERANGE (an id out of
+ * range), BFC_EDUP (a repeated edge without BFC_DEDUP), BFC_ENOMEM, BFC_ECUDA. */
+int bfc_graph_from_edges(const uint32_t *u, const uint32_t *v, uint64_t m, uint32_t nU, uint32_t nV,
+                         uint32_t flags, void *stream, bfc_graph **out);
+
+/* Release a graph and its device memory (after work on its stream is done). */
+int bfc_graph_free(bfc_graph *g);
+
+/* Sizes and degree statistics (host outputs, any may be NULL):
+ *   m, sum_{U} d^2, sum_{V} d^2 (the Table 1 columns), and the wedge count
+ *   W_U = sum_{u in U} C(d_u, 2), W_V = sum_{v in V} C(d_v, 2) (Lemma 2: the
+ *   work of Algorithm 1 is the wedge count of the side that does NOT start). */
+int bfc_graph_stats(const bfc_graph *g, uint64_t *m, uint64_t *sq_u, uint64_t *sq_v, uint64_t *wedges_u,
+                    uint64_t *wedges_v);
+
+/* Copy the canonical edge list out (device outputs, each of length m):
+ * edge e of the canonical order is (u_out[e], v_out[e]).  Either may be NULL. */
+int bfc_graph_edges(const bfc_graph *g, uint32_t *u_out, uint32_t *v_out, void *stream);
+
+/* ---- exact counting (Section 4) --------------------------------------- */
+
+/* ExactBFC (Algorithm 1; Lemma 1 Eq. (3)): B(G) into *out_B (host).
+ * flags: one of BFC_SIDE_AUTO / BFC_SIDE_U / BFC_SIDE_V selects the start
+ * side; the count does not depend on it, the work does (Lemma 2).
+ * *out_side (host, may be NULL) receives 0 if U started, 1 if V.
+ * Each unordered pair of start vertices is counted once (the ordering of
+ * Algorithm 1's coloured line), so no halving is needed.
+ * Errors: BFC_EINVAL, BFC_ECUDA, BFC_ETIMEOUT, BFC_EOVERFLOW. */
+int bfc_exact(bfc_graph *g, uint32_t flags, uint64_t *out_B, int *out_side, void *stream);
+
+/* vBFC for every vertex (Algorithm 2; Lemma 1 Eq. (2)).
+ *   bU : device, nU entries, b_u for u in U
+ *   bV : device, nV entries, b_v for v in V
+ *   out_B (host, may be NULL): B.
+ * Either array may be NULL to skip it (its side's work is still done). */
+int bfc_per_vertex(bfc_graph *g, uint32_t flags, uint64_t *bU, uint64_t *bV, uint64_t *out_B, void *stream);
+
+/* eBFC for every edge: be[e] (device, m entries, canonical order) = number of
+ * butterflies containing edge e (Section 2 definition; computed as
+ * b_(a,x) = sum over the other endpoint w of x of (|Gamma_a ^ Gamma_w| - 1)).
+ * out_B (host, may be NULL): B. */
+int bfc_per_edge(bfc_graph *g, uint32_t flags, uint64_t *be, uint64_t *out_B, void *stream);
+
+/* ---- sparsification (Section 6) --------------------------------------- */
+
+/* ESpar (Algorithm 8), `trials` independent trials.  Trial t keeps canonical
+ * edge e iff hi32(SplitMix64 output e+1 of the sequence seeded by s_t) < T,
+ * T = floor(p * 2^32), s_t = output t+1 of the sequence seeded by `seed`
+ * (SplitMix64: Steele, Lea, Flood, OOPSLA 2014).  beta_t = ExactBFC(E'_t);
+ * est_t = beta_t * (2^32 / T)^4, which is unbiased for the rounded p.
+ *   est  : host, trials doubles (may be NULL)
+ *   beta : host, trials uint64 (may be NULL)
+ * Errors: BFC_EINVAL (p <= 0, p >= 1 or T == 0, trials == 0). */
+int bfc_espar(bfc_graph *g, double p, uint32_t trials, uint64_t seed, double *est, uint64_t *beta,
+              void *stream);
+
+/* ClrSpar (Algorithm 9): colour c_t(x) in [0, N) of a vertex is
+ * (hi32(output k of s_t's sequence) * N) >> 32, with k = u + 1 for u in U and
+ * k = nU + v + 1 for v in V; keep the edges whose ends share a colour;
+ * est_t = beta_t * N^3.  Outputs as bfc_espar.  Errors: BFC_EINVAL (N == 0). */
+int bfc_clrspar(bfc_graph *g, uint32_t colors, uint32_t trials, uint64_t seed, double *est, uint64_t *beta,
+                void *stream);
+
+/* ---- vertex sampling (Section 5.1) ------------------------------------- */
+
+/* VSamp (Algorithm 4), `trials` trials of k draws each over the population
+ * V = U u V (n = nU + nV; population index i < nU is U vertex i, else V vertex
+ * i - nU).  Draw j of trial t uses outputs 2j+1 (r1) and 2j+2 (r2) of s_t's
+ * sequence.
+ *   prop == NULL : uniform, index = mulhi64(r2, n), q = 1/n; the draw's term is
+ *                  b * n / 4 (Algorithm 4's return value).
+ *   prop != NULL : the mixture q(i) = 1/(2n) + w_i / (2 W) over the proposal's
+ *                  integer weights w (W = sum w); top bit of r1 = 0 -> uniform
+ *                  index as above, 1 -> first i with w_0+..+w_i > mulhi64(r2, W).
+ *                  The draw's term is b / (4 q) (importance weighting, so the
+ *                  estimator stays unbiased).
+ *   est : host, trials doubles: the mean of the k terms of each trial.
+ *   drawn : device, trials*k uint64 population indices (may be NULL).
+ *   bdraw : device, trials*k uint64 counts b of the draws (may be NULL). */
+int bfc_vsamp(bfc_graph *g, uint64_t k, const bfc_proposal *prop, uint32_t trials, uint64_t seed,
+              double *est, uint64_t *drawn, uint64_t *bdraw, void *stream);
+
+/* A sampling proposal from integer weights (device or host per flags
+ * BFC_INPUT_DEVICE), one per population index (nU + nV entries, U first).
+ * The weights are copied; W = sum must be > 0. */
+int bfc_proposal_from_weights(bfc_graph *g, const uint32_t *weights, uint32_t flags, void *stream,
+                              bfc_proposal **out);
+int bfc_proposal_free(bfc_proposal *p);
+
+/* ---- misc -------------------------------------------------------------- */
+const char *bfc_strerror(int code);
+/* Number of kernel launches this library has made on the calling thread's
+ * behalf since load (for launch accounting in benchmarks). */
+uint64_t bfc_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BFC_H */

@@ -1,0 +1,281 @@
+"""Thin ctypes binding of libbfc.so (include/bfc.h).
+
+Argument marshalling only: every step of the counting path runs in the CUDA
+library.  The functions keep the C names (bfc_graph_from_edges, bfc_exact,
+...); :class:`Graph` wraps a handle for convenience.  There is no fallback: if
+the library is missing or fails to load, every call raises.
+
+Device arrays are torch CUDA tensors (torch is used for device memory and
+streams only).  uint64 counts are returned in int64 tensors holding the same
+bits (every count here is below 2^63).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbfc.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "bfc.h")
+
+BFC_OK = 0
+BFC_INPUT_DEVICE = 0x1
+BFC_DEDUP = 0x2
+BFC_SIDE_AUTO = 0x0
+BFC_SIDE_U = 0x10
+BFC_SIDE_V = 0x20
+
+_lib = None
+
+
+class BfcError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libbfc.so; raise if it is not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it first (python -m paper_1801_00338_gb300.build)")
+    L = ctypes.CDLL(path)
+    P, u32, u64, i32, dbl = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_double
+    sig = {
+        "bfc_graph_from_edges": [P, P, u64, u32, u32, u32, P, P],
+        "bfc_graph_free": [P],
+        "bfc_graph_stats": [P, P, P, P, P, P],
+        "bfc_graph_edges": [P, P, P, P],
+        "bfc_exact": [P, u32, P, P, P],
+        "bfc_per_vertex": [P, u32, P, P, P, P],
+        "bfc_per_edge": [P, u32, P, P, P],
+        "bfc_espar": [P, dbl, u32, u64, P, P, P],
+        "bfc_clrspar": [P, u32, u32, u64, P, P, P],
+        "bfc_vsamp": [P, u64, P, u32, u64, P, P, P, P],
+        "bfc_proposal_from_weights": [P, P, u32, P, P],
+        "bfc_proposal_free": [P],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = i32
+    L.bfc_strerror.argtypes = [i32]
+    L.bfc_strerror.restype = ctypes.c_char_p
+    L.bfc_launch_count.argtypes = []
+    L.bfc_launch_count.restype = u64
+    _lib = L
+    return L
+
+
+def header_symbols(path: str = HEADER) -> list[str]:
+    """Every function the public header declares."""
+    txt = open(path).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char \*|uint64_t)\s*(bfc_\w+)\s*\(", txt, re.M)))
+
+
+def strerror(code: int) -> str:
+    return load().bfc_strerror(code).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != BFC_OK:
+        raise BfcError(rc, what)
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream or None
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+def _dptr(t) -> int:
+    return t.data_ptr()
+
+
+def bfc_launch_count() -> int:
+    return int(load().bfc_launch_count())
+
+
+# ----------------------------------------------------------------------------
+# C-named entry points
+# ----------------------------------------------------------------------------
+
+def bfc_graph_from_edges(u, v, nU: int, nV: int, flags: int = 0, stream=None) -> int:
+    """Build a graph; u, v are host numpy uint32 arrays or CUDA uint32/int32 tensors."""
+    L = load()
+    h = ctypes.c_void_p()
+    if hasattr(u, "is_cuda") and u.is_cuda:
+        import torch
+        if u.dtype not in (torch.int32, torch.uint32) or v.dtype != u.dtype:
+            raise TypeError("device edge arrays must be int32/uint32 tensors")
+        u = u.contiguous()
+        v = v.contiguous()
+        m = u.numel()
+        rc = L.bfc_graph_from_edges(_dptr(u), _dptr(v), m, nU, nV, flags | BFC_INPUT_DEVICE, _stream_ptr(stream),
+                                    ctypes.byref(h))
+    else:
+        u = np.ascontiguousarray(u, dtype=np.uint32)
+        v = np.ascontiguousarray(v, dtype=np.uint32)
+        if u.size != v.size:
+            raise ValueError("u and v differ in length")
+        rc = L.bfc_graph_from_edges(u.ctypes.data, v.ctypes.data, u.size, nU, nV, flags & ~BFC_INPUT_DEVICE,
+                                    _stream_ptr(stream), ctypes.byref(h))
+    _check(rc, "bfc_graph_from_edges")
+    return h.value
+
+
+def bfc_graph_free(h: int):
+    _check(load().bfc_graph_free(h), "bfc_graph_free")
+
+
+def bfc_graph_stats(h: int) -> dict:
+    vals = [ctypes.c_uint64() for _ in range(5)]
+    _check(load().bfc_graph_stats(h, *[ctypes.byref(x) for x in vals]), "bfc_graph_stats")
+    keys = ("m", "sq_u", "sq_v", "wedges_u", "wedges_v")
+    return {k: int(x.value) for k, x in zip(keys, vals)}
+
+
+def bfc_graph_edges(h: int, m: int, stream=None):
+    import torch
+    u = torch.empty(m, dtype=torch.int32, device="cuda")
+    v = torch.empty(m, dtype=torch.int32, device="cuda")
+    _check(load().bfc_graph_edges(h, _dptr(u), _dptr(v), _stream_ptr(stream)), "bfc_graph_edges")
+    return u, v
+
+
+def bfc_exact(h: int, flags: int = 0, stream=None) -> tuple[int, int]:
+    B = ctypes.c_uint64()
+    side = ctypes.c_int()
+    _check(load().bfc_exact(h, flags, ctypes.byref(B), ctypes.byref(side), _stream_ptr(stream)), "bfc_exact")
+    return int(B.value), int(side.value)
+
+
+def bfc_per_vertex(h: int, nU: int, nV: int, flags: int = 0, stream=None):
+    import torch
+    bU = torch.empty(nU, dtype=torch.int64, device="cuda")
+    bV = torch.empty(nV, dtype=torch.int64, device="cuda")
+    B = ctypes.c_uint64()
+    _check(load().bfc_per_vertex(h, flags, _dptr(bU), _dptr(bV), ctypes.byref(B), _stream_ptr(stream)),
+           "bfc_per_vertex")
+    return bU, bV, int(B.value)
+
+
+def bfc_per_edge(h: int, m: int, flags: int = 0, stream=None):
+    import torch
+    be = torch.empty(max(m, 1), dtype=torch.int64, device="cuda")
+    B = ctypes.c_uint64()
+    _check(load().bfc_per_edge(h, flags, _dptr(be), ctypes.byref(B), _stream_ptr(stream)), "bfc_per_edge")
+    return be[:m], int(B.value)
+
+
+def bfc_espar(h: int, p: float, trials: int, seed: int, stream=None):
+    est = np.zeros(trials, np.float64)
+    beta = np.zeros(trials, np.uint64)
+    _check(load().bfc_espar(h, p, trials, seed & 0xFFFFFFFFFFFFFFFF, est.ctypes.data, beta.ctypes.data,
+                            _stream_ptr(stream)), "bfc_espar")
+    return est, beta
+
+
+def bfc_clrspar(h: int, colors: int, trials: int, seed: int, stream=None):
+    est = np.zeros(trials, np.float64)
+    beta = np.zeros(trials, np.uint64)
+    _check(load().bfc_clrspar(h, colors, trials, seed & 0xFFFFFFFFFFFFFFFF, est.ctypes.data, beta.ctypes.data,
+                              _stream_ptr(stream)), "bfc_clrspar")
+    return est, beta
+
+
+def bfc_proposal_from_weights(h: int, weights, stream=None) -> int:
+    L = load()
+    p = ctypes.c_void_p()
+    if hasattr(weights, "is_cuda") and weights.is_cuda:
+        rc = L.bfc_proposal_from_weights(h, _dptr(weights.contiguous()), BFC_INPUT_DEVICE, _stream_ptr(stream),
+                                         ctypes.byref(p))
+    else:
+        w = np.ascontiguousarray(weights, dtype=np.uint32)
+        rc = L.bfc_proposal_from_weights(h, w.ctypes.data, 0, _stream_ptr(stream), ctypes.byref(p))
+    _check(rc, "bfc_proposal_from_weights")
+    return p.value
+
+
+def bfc_proposal_free(p: int):
+    _check(load().bfc_proposal_free(p), "bfc_proposal_free")
+
+
+def bfc_vsamp(h: int, k: int, trials: int, seed: int, proposal: int | None = None, want_draws: bool = False,
+              stream=None):
+    import torch
+    est = np.zeros(trials, np.float64)
+    drawn = bd = None
+    pd = pb = None
+    if want_draws:
+        drawn = torch.empty(max(trials * k, 1), dtype=torch.int64, device="cuda")
+        bd = torch.empty(max(trials * k, 1), dtype=torch.int64, device="cuda")
+        pd, pb = _dptr(drawn), _dptr(bd)
+    _check(load().bfc_vsamp(h, k, proposal, trials, seed & 0xFFFFFFFFFFFFFFFF, est.ctypes.data, pd, pb,
+                            _stream_ptr(stream)), "bfc_vsamp")
+    if want_draws:
+        return est, drawn[: trials * k], bd[: trials * k]
+    return est
+
+
+# ----------------------------------------------------------------------------
+# convenience wrapper
+# ----------------------------------------------------------------------------
+
+_SIDE = {None: BFC_SIDE_AUTO, "auto": BFC_SIDE_AUTO, "U": BFC_SIDE_U, "V": BFC_SIDE_V, 0: BFC_SIDE_U, 1: BFC_SIDE_V}
+
+
+class Graph:
+    """A bipartite graph resident on the GPU (a bfc_graph handle)."""
+
+    def __init__(self, u, v, nU: int, nV: int, dedup: bool = False, stream=None):
+        self.nU, self.nV = int(nU), int(nV)
+        self.h = bfc_graph_from_edges(u, v, nU, nV, BFC_DEDUP if dedup else 0, stream)
+        self.stats = bfc_graph_stats(self.h)
+        self.m = self.stats["m"]
+
+    def exact(self, side=None, stream=None):
+        return bfc_exact(self.h, _SIDE[side], stream)
+
+    def per_vertex(self, side=None, stream=None):
+        return bfc_per_vertex(self.h, self.nU, self.nV, _SIDE[side], stream)
+
+    def per_edge(self, side=None, stream=None):
+        return bfc_per_edge(self.h, self.m, _SIDE[side], stream)
+
+    def edges(self, stream=None):
+        return bfc_graph_edges(self.h, self.m, stream)
+
+    def espar(self, p, trials, seed, stream=None):
+        return bfc_espar(self.h, p, trials, seed, stream)
+
+    def clrspar(self, colors, trials, seed, stream=None):
+        return bfc_clrspar(self.h, colors, trials, seed, stream)
+
+    def vsamp(self, k, trials, seed, proposal=None, want_draws=False, stream=None):
+        return bfc_vsamp(self.h, k, trials, seed, proposal, want_draws, stream)
+
+    def close(self):
+        if self.h:
+            bfc_graph_free(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

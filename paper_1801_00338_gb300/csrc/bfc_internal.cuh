@@ -1,0 +1,161 @@
+// Internal declarations of the butterfly-counting library (not installed).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/bfc.h"
+
+namespace bfc {
+
+// ---------------------------------------------------------------------------
+// status handling
+// ---------------------------------------------------------------------------
+struct Status {
+  int code = BFC_OK;
+  bool ok() const { return code == BFC_OK; }
+};
+
+#define BFC_CUDA_TRY(expr)                                        \
+  do {                                                            \
+    cudaError_t _e = (expr);                                      \
+    if (_e != cudaSuccess) {                                      \
+      bfc::note_cuda_error(_e, #expr, __FILE__, __LINE__);        \
+      return (_e == cudaErrorMemoryAllocation) ? BFC_ENOMEM : BFC_ECUDA; \
+    }                                                             \
+  } while (0)
+
+#define BFC_TRY(expr)          \
+  do {                         \
+    int _rc = (expr);          \
+    if (_rc != BFC_OK) return _rc; \
+  } while (0)
+
+void note_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+void count_launch(uint64_t n = 1);
+
+// Check the launch that was just made.
+#define BFC_LAUNCHED()                     \
+  do {                                     \
+    bfc::count_launch();                   \
+    BFC_CUDA_TRY(cudaGetLastError());      \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// device-side error word: kernels set bits, the host reads it after a call
+// ---------------------------------------------------------------------------
+enum DeviceError : uint32_t {
+  DERR_NONE = 0,
+  DERR_RANGE = 1u << 0,      // an id out of range
+  DERR_DUP = 1u << 1,        // a duplicate edge
+  DERR_CAPACITY = 1u << 2,   // a table ran out of room (internal consistency)
+  DERR_TIMEOUT = 1u << 3,    // a bounded wait gave up
+  DERR_OVERFLOW = 1u << 4,   // a counter would have wrapped
+};
+
+// ---------------------------------------------------------------------------
+// stream-ordered device buffers
+// ---------------------------------------------------------------------------
+struct DBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+int dalloc(DBuf &b, size_t bytes, cudaStream_t s);
+void dfree(DBuf &b, cudaStream_t s);
+template <class T>
+T *ptr(const DBuf &b) { return static_cast<T *>(b.p); }
+
+// Scratch arena grown on demand (stream ordered), used by one call at a time.
+struct Scratch {
+  DBuf buf;
+  int reserve(size_t bytes, cudaStream_t s);
+  void *base() const { return buf.p; }
+};
+
+// ---------------------------------------------------------------------------
+// primitives (primitives.cu)
+// ---------------------------------------------------------------------------
+// Exclusive scan of n values into out[0..n] (out[n] = total).  in may alias out
+// only if it is not used afterwards.
+int exclusive_scan_u32_to_u64(const uint32_t *in, uint64_t *out, uint64_t n, Scratch &scr, cudaStream_t s);
+int exclusive_scan_u64(const uint64_t *in, uint64_t *out, uint64_t n, Scratch &scr, cudaStream_t s);
+
+// Stable LSD radix sort of (key, value) pairs over key bits [0, end_bit).
+// Buffers: keys/vals are double buffers; the result ends in *_out after the
+// call (the functions ping-pong internally and copy when needed).
+int radix_sort_u64(const uint64_t *keys_in, uint64_t *keys_out, const uint32_t *vals_in, uint32_t *vals_out,
+                   uint64_t n, int end_bit, Scratch &scr, cudaStream_t s);
+int radix_sort_u32(const uint32_t *keys_in, uint32_t *keys_out, const uint32_t *vals_in, uint32_t *vals_out,
+                   uint64_t n, int end_bit, Scratch &scr, cudaStream_t s);
+
+int bits_for(uint64_t max_value);  // number of bits to represent max_value (0 -> 0)
+
+// sum of a u64 array into one device word (added to *out)
+int reduce_add_u64(const uint64_t *in, uint64_t n, unsigned long long *out, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// graph (graph.cu)
+// ---------------------------------------------------------------------------
+// Per-start-side layout for wedge aggregation ("plan").  Start vertices are
+// renumbered by rank: ascending degree, ties by id.  The total order "w after
+// v" of Algorithm 1's coloured line is rank(w) > rank(v).
+struct Plan {
+  bool built = false;
+  int side = 0;          // 0: U starts, 1: V starts
+  uint32_t nS = 0, nM = 0;
+  uint64_t m = 0;
+  DBuf vert_of;          // u32[nS]  vertex id at rank r
+  DBuf rank_of;          // u32[nS]  rank of vertex id
+  DBuf offR;             // u64[nS+1] start rows in rank order
+  DBuf sX;               // u32[m]   midpoint of each start-row entry
+  DBuf sEid;             // u32[m]   canonical id of that edge
+  DBuf sB;               // u32[m]   index in mR just after this edge (suffix begin)
+  DBuf mR;               // u32[m]   midpoint rows (offsets offM): start ranks, ascending
+  DBuf mEid;             // u32[m]   canonical id of each midpoint-row entry
+  const uint64_t *offM = nullptr;  // midpoint row offsets (the graph's, or offM_own)
+  DBuf offM_own;         // u64[nM+1] for a filtered (sparsified) plan
+  DBuf work;             // u64[nS]  ordered wedges walked from each start rank
+  // vertex classes (ranks), see wedge.cu
+  DBuf cls;              // u32[nS]  ranks grouped by class
+  uint32_t cls_count[4] = {0, 0, 0, 0};
+  uint32_t cls_begin[4] = {0, 0, 0, 0};
+  uint64_t total_work = 0;     // sum of work = W of the midpoint side
+  uint32_t max_deg_S = 0;
+};
+
+}  // namespace bfc
+
+struct bfc_graph {
+  uint32_t nU = 0, nV = 0;
+  uint64_t m = 0;
+  bfc::DBuf offU, nbrU;        // u64[nU+1], u32[m] (canonical order)
+  bfc::DBuf offV, nbrV, eidV;  // u64[nV+1], u32[m], u32[m]
+  bfc::DBuf degU, degV;        // u32
+  uint64_t sqU = 0, sqV = 0, wU = 0, wV = 0;
+  uint32_t maxU = 0, maxV = 0;
+  bfc::Plan plan[2];
+  bfc::Scratch scr;
+  bfc::DBuf err;               // u32 device error word
+  bfc::DBuf acc;               // u64 accumulators (small)
+  cudaStream_t last_stream = nullptr;
+};
+
+namespace bfc {
+int graph_build(bfc_graph *g, const uint32_t *u, const uint32_t *v, uint64_t m, uint32_t flags, cudaStream_t s);
+int plan_build(bfc_graph *g, int side, cudaStream_t s);
+int choose_side(const bfc_graph *g, uint32_t flags);
+int read_device_error(bfc_graph *g, cudaStream_t s);  // maps DERR_* bits to a status and clears
+
+// wedge.cu
+enum Mode { MODE_TOTAL = 0, MODE_VERTEX = 1, MODE_EDGE = 2 };
+// Counts with the start side of plan p.  out_B receives B (device u64).
+// bS / bM: per-vertex outputs of the start / midpoint side (device, original
+// ids) or null; be: per-edge output (canonical ids) or null.
+int wedge_count(bfc_graph *g, Plan &p, Mode mode, unsigned long long *d_B, uint64_t *bS, uint64_t *bM,
+                uint64_t *be, cudaStream_t s);
+int plan_classify(bfc_graph *g, Plan &p, cudaStream_t s);
+void plan_free(Plan &p, cudaStream_t s);
+// Filter plan `parent` to the canonical edges with keep[e] != 0 into `out`
+// (same start side and rank order; rows stay sorted).
+int plan_filter(bfc_graph *g, const Plan &parent, const uint32_t *keep, Plan &out, cudaStream_t s);
+}  // namespace bfc

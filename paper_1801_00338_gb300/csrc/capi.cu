@@ -1,0 +1,163 @@
+// C ABI entry points (declared in include/bfc.h).
+#include <new>
+
+#include "bfc_internal.cuh"
+
+using namespace bfc;
+
+namespace {
+
+cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// device accumulator layout inside g->acc (256 bytes):
+//   [0, 8)   B
+//   [64, 72) work queues (2 x u32)
+unsigned long long *acc_B(bfc_graph *g) { return ptr<unsigned long long>(g->acc); }
+
+__global__ void k_rows_to_ids(const uint64_t *off, uint32_t n, uint32_t *out) {
+  const int lane = threadIdx.x & 31;
+  uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t r = warp; r < n; r += nw)
+    for (uint64_t e = off[r] + lane; e < off[r + 1]; e += 32) out[e] = (uint32_t)r;
+}
+
+int finish_count(bfc_graph *g, uint64_t *out_B, cudaStream_t s) {
+  unsigned long long hB = 0;
+  if (out_B) BFC_CUDA_TRY(cudaMemcpyAsync(&hB, acc_B(g), 8, cudaMemcpyDeviceToHost, s));
+  BFC_TRY(read_device_error(g, s));  // synchronises s
+  if (out_B) *out_B = hB;
+  return BFC_OK;
+}
+
+int prepare(bfc_graph *g, uint32_t flags, cudaStream_t s, int *side) {
+  if (!g) return BFC_EINVAL;
+  if ((flags & BFC_SIDE_U) && (flags & BFC_SIDE_V)) return BFC_EINVAL;
+  *side = choose_side(g, flags);
+  BFC_TRY(plan_build(g, *side, s));
+  g->last_stream = s;
+  BFC_CUDA_TRY(cudaMemsetAsync(acc_B(g), 0, 8, s));
+  return BFC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bfc_graph_from_edges(const uint32_t *u, const uint32_t *v, uint64_t m, uint32_t nU, uint32_t nV, uint32_t flags,
+                         void *stream, bfc_graph **out) {
+  if (!out || nU == 0 || nV == 0) return BFC_EINVAL;
+  if (m > 0 && (!u || !v)) return BFC_EINVAL;
+  if (flags & ~(BFC_INPUT_DEVICE | BFC_DEDUP)) return BFC_EINVAL;
+  if (m >= (1ull << 32)) return BFC_ERANGE;
+  *out = nullptr;
+  bfc_graph *g = new (std::nothrow) bfc_graph();
+  if (!g) return BFC_ENOMEM;
+  g->nU = nU;
+  g->nV = nV;
+  cudaStream_t s = as_stream(stream);
+  g->last_stream = s;
+  int rc = graph_build(g, u, v, m, flags, s);
+  if (rc != BFC_OK) {
+    bfc_graph_free(g);
+    return rc;
+  }
+  *out = g;
+  return BFC_OK;
+}
+
+int bfc_graph_free(bfc_graph *g) {
+  if (!g) return BFC_EINVAL;
+  cudaStream_t s = g->last_stream;
+  cudaStreamSynchronize(s);
+  for (int side = 0; side < 2; side++) {
+    Plan &p = g->plan[side];
+    DBuf *bufs[] = {&p.vert_of, &p.rank_of, &p.offR, &p.sX, &p.sEid, &p.sB, &p.mR, &p.mEid, &p.work, &p.cls};
+    for (DBuf *b : bufs) dfree(*b, s);
+  }
+  DBuf *gb[] = {&g->offU, &g->nbrU, &g->offV, &g->nbrV, &g->eidV, &g->degU, &g->degV, &g->err, &g->acc, &g->scr.buf};
+  for (DBuf *b : gb) dfree(*b, s);
+  cudaStreamSynchronize(s);
+  delete g;
+  return BFC_OK;
+}
+
+int bfc_graph_stats(const bfc_graph *g, uint64_t *m, uint64_t *sq_u, uint64_t *sq_v, uint64_t *wedges_u,
+                    uint64_t *wedges_v) {
+  if (!g) return BFC_EINVAL;
+  if (m) *m = g->m;
+  if (sq_u) *sq_u = g->sqU;
+  if (sq_v) *sq_v = g->sqV;
+  if (wedges_u) *wedges_u = g->wU;
+  if (wedges_v) *wedges_v = g->wV;
+  return BFC_OK;
+}
+
+int bfc_graph_edges(const bfc_graph *g, uint32_t *u_out, uint32_t *v_out, void *stream) {
+  if (!g) return BFC_EINVAL;
+  cudaStream_t s = as_stream(stream);
+  if (g->m == 0) return BFC_OK;
+  if (u_out) {
+    unsigned grid = (unsigned)std::min<uint64_t>(((uint64_t)g->nU * 32 + 255) / 256, 152 * 16);
+    k_rows_to_ids<<<grid ? grid : 1, 256, 0, s>>>(ptr<uint64_t>(g->offU), g->nU, u_out);
+    BFC_LAUNCHED();
+  }
+  if (v_out) BFC_CUDA_TRY(cudaMemcpyAsync(v_out, g->nbrU.p, g->m * 4, cudaMemcpyDeviceToDevice, s));
+  return BFC_OK;
+}
+
+int bfc_exact(bfc_graph *g, uint32_t flags, uint64_t *out_B, int *out_side, void *stream) {
+  if (!out_B) return BFC_EINVAL;
+  cudaStream_t s = as_stream(stream);
+  int side = 0;
+  BFC_TRY(prepare(g, flags, s, &side));
+  BFC_TRY(wedge_count(g, g->plan[side], MODE_TOTAL, acc_B(g), nullptr, nullptr, nullptr, s));
+  BFC_TRY(finish_count(g, out_B, s));
+  if (out_side) *out_side = side;
+  return BFC_OK;
+}
+
+int bfc_per_vertex(bfc_graph *g, uint32_t flags, uint64_t *bU, uint64_t *bV, uint64_t *out_B, void *stream) {
+  cudaStream_t s = as_stream(stream);
+  int side = 0;
+  BFC_TRY(prepare(g, flags, s, &side));
+  DBuf tmpU, tmpV;
+  if (!bU) BFC_TRY(dalloc(tmpU, (uint64_t)g->nU * 8, s));
+  if (!bV) BFC_TRY(dalloc(tmpV, (uint64_t)g->nV * 8, s));
+  uint64_t *pU = bU ? bU : ptr<uint64_t>(tmpU);
+  uint64_t *pV = bV ? bV : ptr<uint64_t>(tmpV);
+  BFC_CUDA_TRY(cudaMemsetAsync(pU, 0, (uint64_t)g->nU * 8, s));
+  BFC_CUDA_TRY(cudaMemsetAsync(pV, 0, (uint64_t)g->nV * 8, s));
+  int rc = wedge_count(g, g->plan[side], MODE_VERTEX, acc_B(g), side ? pV : pU, side ? pU : pV, nullptr, s);
+  if (rc == BFC_OK) rc = finish_count(g, out_B, s);
+  dfree(tmpU, s);
+  dfree(tmpV, s);
+  return rc;
+}
+
+int bfc_per_edge(bfc_graph *g, uint32_t flags, uint64_t *be, uint64_t *out_B, void *stream) {
+  if (!be && g && g->m > 0) return BFC_EINVAL;
+  cudaStream_t s = as_stream(stream);
+  int side = 0;
+  BFC_TRY(prepare(g, flags, s, &side));
+  if (g->m > 0) BFC_CUDA_TRY(cudaMemsetAsync(be, 0, g->m * 8, s));
+  BFC_TRY(wedge_count(g, g->plan[side], MODE_EDGE, acc_B(g), nullptr, nullptr, be, s));
+  return finish_count(g, out_B, s);
+}
+
+const char *bfc_strerror(int code) {
+  switch (code) {
+    case BFC_OK: return "ok";
+    case BFC_EINVAL: return "invalid argument";
+    case BFC_ERANGE: return "vertex id or size out of range";
+    case BFC_EDUP: return "duplicate edge";
+    case BFC_ENOMEM: return "out of memory";
+    case BFC_ECUDA: return "CUDA runtime error";
+    case BFC_ETIMEOUT: return "device wait timed out";
+    case BFC_EOVERFLOW: return "integer overflow";
+    case BFC_EINTERNAL: return "internal consistency check failed";
+  }
+  return "unknown error";
+}
+
+}  // extern "C"

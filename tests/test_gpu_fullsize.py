@@ -1,0 +1,70 @@
+"""The 1M x 5M, 50M-edge Chung-Lu workload (exponents 2.1 / 2.5), in the launch
+configuration the benchmark times: sampled outputs against the oracle computed
+one by one, and identities that hold at any size."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1801_00338_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def big():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1801_00338_gb300 import build as B
+    B.build()
+    from paper_1801_00338_gb300 import bfc
+    g = synth.chung_lu_1m_5m()
+    G = bfc.Graph(g.u, g.v, g.nU, g.nV)
+    yield g, G
+    G.close()
+
+
+def u64(t):
+    return t.cpu().numpy().view(np.uint64)
+
+
+def test_identities_and_sampled_vertices(big):
+    g, G = big
+    B, side = G.exact()
+    assert side == 0  # sum_U d^2 > sum_V d^2: U starts, wedges are centred on V
+    bU, bV, B2 = G.per_vertex()
+    assert B2 == B
+    bU, bV = u64(bU), u64(bV)
+    assert int(bU.sum()) == 2 * B and int(bV.sum()) == 2 * B
+    dU = np.bincount(g.u, minlength=g.nU)
+    # sample: the 20 highest-degree vertices and 180 spread over the rest, each side
+    idsU = np.unique(np.concatenate([np.argsort(dU)[-20:], np.arange(0, g.nU, g.nU // 180)])).astype(np.uint32)
+    dV = np.bincount(g.v, minlength=g.nV)
+    idsV = np.unique(np.concatenate([np.argsort(dV)[-20:], np.arange(0, g.nV, g.nV // 180)])).astype(np.uint32)
+    assert np.array_equal(bU[idsU], O.per_vertex_list(g.u, g.v, g.nU, g.nV, 0, idsU))
+    assert np.array_equal(bV[idsV], O.per_vertex_list(g.u, g.v, g.nU, g.nV, 1, idsV))
+
+
+def test_per_edge_identities_and_samples(big):
+    g, G = big
+    B, _ = G.exact()
+    be, B3 = G.per_edge()
+    assert B3 == B
+    be = u64(be)
+    assert int(be.sum()) == 4 * B
+    cu, cv = G.edges()
+    cu = cu.cpu().numpy().astype(np.uint32)
+    cv = cv.cpu().numpy().astype(np.uint32)
+    # b_x = 1/2 sum of b_e over x's edges, on the V side
+    bU, bV, _ = G.per_vertex()
+    sV = np.zeros(g.nV, np.uint64)
+    np.add.at(sV, cv, be)
+    assert np.array_equal(sV, 2 * u64(bV))
+    idx = np.arange(0, g.m, g.m // 150, dtype=np.uint64)
+    assert np.array_equal(be[idx.astype(np.int64)], O.per_edge_list(cu, cv, g.nU, g.nV, idx))
+
+
+def test_start_side_invariance(big):
+    g, G = big
+    B, _ = G.exact()
+    assert G.exact("U")[0] == B
+    assert G.exact("V")[0] == B  # 35x the wedges (centred on U), same count

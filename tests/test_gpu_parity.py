@@ -1,0 +1,184 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Counts are integers: every comparison is exact (bit for bit).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1801_00338_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bfc():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1801_00338_gb300 import build as B
+    B.build()
+    from paper_1801_00338_gb300 import bfc as mod
+    mod.load()
+    return mod
+
+
+def u64(t):
+    return t.cpu().numpy().view(np.uint64)
+
+
+def check_all(bfc, u, v, nU, nV, per_edge=True, sides=(None, "U", "V")):
+    oB, oside = O.exact(u, v, nU, nV)
+    with bfc.Graph(u, v, nU, nV) as G:
+        for side in sides:
+            B, s = G.exact(side)
+            assert B == oB, (side, B, oB)
+            if side is None:
+                assert s == oside
+        bU, bV, B2 = G.per_vertex()
+        assert B2 == oB
+        oU, oV = O.per_vertex(u, v, nU, nV)
+        assert np.array_equal(u64(bU), oU)
+        assert np.array_equal(u64(bV), oV)
+        if per_edge:
+            be, B3 = G.per_edge()
+            assert B3 == oB
+            can = O.canonical_ids(u, v, nU, nV)
+            assert np.array_equal(u64(be)[can], O.per_edge(u, v, nU, nV))
+    return oB
+
+
+def test_uniform_2000x3000(bfc):
+    g = synth.uniform_small(1)
+    assert check_all(bfc, g.u, g.v, g.nU, g.nV) > 0
+
+
+def test_tiny_random_graphs(bfc):
+    rs = synth.uniform01(21, 0, 3 * 150).reshape(150, 3)
+    for i in range(150):
+        nU = 1 + int(rs[i, 0] * 12)
+        nV = 1 + int(rs[i, 1] * 12)
+        m = int(rs[i, 2] * nU * nV)
+        if m == 0:
+            continue
+        u, v = synth.uniform_bipartite(nU, nV, m, 500 + i)
+        check_all(bfc, u, v, nU, nV)
+
+
+@pytest.mark.parametrize("a,b", [(2, 2), (3, 40), (40, 3), (700, 30), (10000, 10)])
+def test_bicliques(bfc, a, b):
+    u, v = synth.complete_bipartite(a, b)
+    C2 = lambda k: k * (k - 1) // 2
+    with bfc.Graph(u, v, a, b) as G:
+        for side in (None, "U", "V"):
+            assert G.exact(side)[0] == C2(a) * C2(b)
+        bU, bV, _ = G.per_vertex()
+        assert (u64(bU) == (a - 1) * C2(b)).all() and (u64(bV) == (b - 1) * C2(a)).all()
+        if a * b <= 30000:
+            be, _ = G.per_edge()
+            assert (u64(be) == (a - 1) * (b - 1)).all()
+
+
+def test_table1_biclique_side_and_count(bfc):
+    """Table 1 row 1: (10^4, 10)-biclique, B = 2,249,775,000; Algorithm 1 starts from R (= V)."""
+    u, v = synth.complete_bipartite(10000, 10)
+    with bfc.Graph(u, v, 10000, 10) as G:
+        assert G.stats["sq_u"] == 10 ** 6 and G.stats["sq_v"] == 10 ** 9
+        assert G.exact() == (2249775000, 1)
+
+
+def test_skewed_graph_spanning_several_rank_windows(bfc):
+    """|U| = 120k start vertices (three 48k-rank windows) with a power-law skew, so the
+    warp and CTA classes both run and CTA vertices walk several windows."""
+    g = synth.chung_lu_scaled(120_000, 30_000, 600_000, 2.1, 2.5, 31)
+    check_all(bfc, g.u, g.v, g.nU, g.nV, per_edge=False)
+    with bfc.Graph(g.u, g.v, g.nU, g.nV) as G:
+        be, B = G.per_edge()
+        be = u64(be)
+        assert int(be.sum()) == 4 * B
+        cu, cv = G.edges()
+        cu = cu.cpu().numpy().astype(np.uint32)
+        cv = cv.cpu().numpy().astype(np.uint32)
+        idx = np.arange(0, g.m, 997, dtype=np.uint64)
+        want = O.per_edge_list(cu, cv, g.nU, g.nV, idx)
+        assert np.array_equal(be[idx.astype(np.int64)], want)
+
+
+def test_medium_chung_lu_per_edge(bfc):
+    g = synth.chung_lu_scaled(3000, 9000, 40_000, 2.1, 2.4, 5)
+    check_all(bfc, g.u, g.v, g.nU, g.nV)
+
+
+def test_empty_and_degenerate(bfc):
+    z = np.zeros(0, np.uint32)
+    with bfc.Graph(z, z, 5, 7) as G:
+        assert G.exact()[0] == 0
+        bU, bV, B = G.per_vertex()
+        assert B == 0 and int(u64(bU).sum()) == 0 and int(u64(bV).sum()) == 0
+    one = np.array([0], np.uint32)
+    with bfc.Graph(one, one, 1, 1) as G:
+        assert G.exact()[0] == 0
+    star_u = np.zeros(50, np.uint32)
+    star_v = np.arange(50, dtype=np.uint32)
+    with bfc.Graph(star_u, star_v, 1, 50) as G:
+        assert G.exact()[0] == 0 and G.exact("V")[0] == 0
+
+
+def test_input_errors(bfc):
+    u = np.array([0, 1, 0], np.uint32)
+    v = np.array([0, 1, 0], np.uint32)
+    with pytest.raises(bfc.BfcError) as e:
+        bfc.Graph(u, v, 2, 2)
+    assert e.value.code == -3
+    with bfc.Graph(u, v, 2, 2, dedup=True) as G:
+        assert G.m == 2 and G.exact()[0] == 0
+    with pytest.raises(bfc.BfcError) as e:
+        bfc.Graph(np.array([2], np.uint32), np.array([0], np.uint32), 2, 2)
+    assert e.value.code == -2
+
+
+def test_dedup_matches_oracle_on_deduplicated_edges(bfc):
+    u, v = synth.uniform_bipartite(50, 60, 900, 4)
+    uu = np.concatenate([u, u[:300]])
+    vv = np.concatenate([v, v[:300]])
+    with bfc.Graph(uu, vv, 50, 60, dedup=True) as G:
+        assert G.m == 900
+        assert G.exact()[0] == O.exact(u, v, 50, 60)[0]
+
+
+def test_device_input(bfc):
+    import torch
+    g = synth.uniform_small(3)
+    du = torch.from_numpy(g.u.astype(np.int32)).cuda()
+    dv = torch.from_numpy(g.v.astype(np.int32)).cuda()
+    with bfc.Graph(du, dv, g.nU, g.nV) as G:
+        assert G.exact()[0] == O.exact(g.u, g.v, g.nU, g.nV)[0]
+
+
+def test_canonical_edges(bfc):
+    g = synth.uniform_small(4)
+    with bfc.Graph(g.u, g.v, g.nU, g.nV) as G:
+        cu, cv = G.edges()
+    key = g.u.astype(np.uint64) * np.uint64(g.nV) + g.v
+    srt = np.sort(key)
+    got = cu.cpu().numpy().astype(np.uint64) * np.uint64(g.nV) + cv.cpu().numpy().astype(np.uint64)
+    assert np.array_equal(got, srt)
+
+
+def test_espar_trials_match_oracle(bfc):
+    g = synth.uniform_small(1)
+    with bfc.Graph(g.u, g.v, g.nU, g.nV) as G:
+        est, beta = G.espar(0.3, 6, 1234)
+    for t in range(6):
+        ob, oe = O.espar_trial(g.u, g.v, g.nU, g.nV, 0.3, 1234, t)
+        assert int(beta[t]) == ob
+        assert est[t] == oe
+
+
+def test_clrspar_trials_match_oracle(bfc):
+    g = synth.chung_lu_scaled(3000, 9000, 40_000, 2.1, 2.4, 5)
+    with bfc.Graph(g.u, g.v, g.nU, g.nV) as G:
+        est, beta = G.clrspar(3, 5, 99)
+    for t in range(5):
+        ob, oe = O.clrspar_trial(g.u, g.v, g.nU, g.nV, 3, 99, t)
+        assert int(beta[t]) == ob
+        assert est[t] == oe
