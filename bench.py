@@ -1,0 +1,342 @@
+#!/usr/bin/env python
+"""Benchmark: exact butterfly counting (B, per-vertex b_v, per-edge b_e) of the
+Chung-Lu bipartite graph |U| = 1M, |V| = 5M, 50M distinct edges, exponents
+2.1 (U) / 2.5 (V), on one GB300 per rank.
+
+One step = the whole counting path on the device-resident edge list: graph
+build (sort, validate, both adjacency structures), degree statistics and side
+choice (Algorithm 1), rank layout and classes, ExactBFC (B), vBFC for every
+vertex and eBFC for every edge.  Metric: wedges/s, where a step's wedges are
+W = sum over the midpoint side of C(d, 2) (Lemma 2: the work of Algorithm 1).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl own|reference]
+
+Under torchrun (N > 1) every rank runs the same workload on its own GPU
+(replicas); value = N * W / max-over-ranks step time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "exact-count wedges/s on 1 GB300; rel. error at equal time, learned vs uniform VSamp"
+WORKLOAD = "chung_lu_U1M_V5M_E50M_g2.1_2.5_seed2: ExactBFC + vBFC + eBFC"
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms during the timed region."""
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={CLOCK_FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload():
+    from paper_1801_00338_gb300 import synth
+    return synth.chung_lu_1m_5m()
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle timing (the baseline; never the target)
+# ----------------------------------------------------------------------------
+
+def oracle_sample(g, side: int, budget_s: float, prepared=None):
+    """Time the oracle's Algorithm 1 loops over start vertices spread evenly over
+    the start side until about budget_s of CPU time.  Returns (wedges/s in units
+    of W, description, prepared handle)."""
+    import oracle as O
+    n = g.nU if side == 0 else g.nV
+    P = prepared or O.Prepared(g.u, g.v, g.nU, g.nV, side)
+    order = np.argsort(O_sample_keys(n)).astype(np.uint32)
+    done, paths, t0 = 0, 0, time.perf_counter()
+    batch = 256
+    while time.perf_counter() - t0 < budget_s and done < n:
+        ids = order[done:done + batch]
+        _, w = P.count(ids)
+        paths += w
+        done += ids.size
+        batch = min(batch * 2, 65536)
+    dt = time.perf_counter() - t0
+    # the unordered loops walk every wedge from both ends: W-units = paths / 2
+    val = (paths / 2.0) / dt
+    desc = (f"{done} of {n} start vertices (uniform random order, seed 7) of the same graph, "
+            f"single-threaded C oracle, {paths} 2-paths in {dt:.1f} s")
+    return val, desc, P
+
+
+def O_sample_keys(n):
+    from paper_1801_00338_gb300 import synth
+    return synth.splitmix64(7, 0, n)
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    g = workload()
+    from paper_1801_00338_gb300 import synth  # noqa: F401
+    # the start side by Algorithm 1 (host arithmetic on degrees, oracle-independent of the GPU)
+    dU = np.bincount(g.u, minlength=g.nU).astype(np.float64)
+    dV = np.bincount(g.v, minlength=g.nV).astype(np.float64)
+    side = 1 if (dU * dU).sum() < (dV * dV).sum() else 0
+    mid_deg = dV if side == 0 else dU
+    W = float((mid_deg * (mid_deg - 1) / 2).sum())
+    P = None
+    per_step = 6.0
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, desc, P = oracle_sample(g, side, per_step, P)
+        if i >= args.warmup:
+            vals.append(v)
+    value = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "wedges/s", "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": W / value * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "W": int(W)},
+        "cpu_baseline": {"value": value, "unit": "wedges/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "wedges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+
+def run_own(args, rank, world, local_rank):
+    import torch
+
+    from paper_1801_00338_gb300 import bfc
+    from paper_1801_00338_gb300 import build as B
+
+    B.build()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    g = workload()
+    nU, nV, m = g.nU, g.nV, g.m
+    du = torch.from_numpy(g.u.astype(np.int32)).cuda()
+    dv = torch.from_numpy(g.v.astype(np.int32)).cuda()
+    bU = torch.empty(nU, dtype=torch.int64, device="cuda")
+    bV = torch.empty(nV, dtype=torch.int64, device="cuda")
+    be = torch.empty(m, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    L = bfc.load()
+    import ctypes
+
+    Bh = ctypes.c_uint64()
+    side_h = ctypes.c_int()
+
+    def step():
+        h = bfc.bfc_graph_from_edges(du, dv, nU, nV, 0, sptr)
+        try:
+            bfc._check(L.bfc_exact(h, 0, ctypes.byref(Bh), ctypes.byref(side_h), sptr), "bfc_exact")
+            bfc._check(L.bfc_per_vertex(h, 0, bU.data_ptr(), bV.data_ptr(), None, sptr), "bfc_per_vertex")
+            bfc._check(L.bfc_per_edge(h, 0, be.data_ptr(), None, sptr), "bfc_per_edge")
+        finally:
+            bfc.bfc_graph_free(h)
+        return int(Bh.value), int(side_h.value)
+
+    # statistics of the workload (not timed)
+    G = bfc.Graph(du, dv, nU, nV)
+    Bval, side = G.exact()
+    st = G.stats
+    W = st["wedges_v"] if side == 0 else st["wedges_u"]
+    ps = G.plan_stats(side)
+    G.close()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    bfc.bfc_profile_reset()
+    bfc.bfc_profile_enable(True)
+    launches0 = bfc.bfc_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        barrier()
+    launches = bfc.bfc_launch_count() - launches0
+    bfc.bfc_profile_enable(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    prof = {t: bfc.bfc_profile_read(t) for t in bfc.PROFILE_TAGS}
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * W / (ms / 1e3)
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies timed
+    hu = torch.from_numpy(g.u.astype(np.int32)).pin_memory()
+    hv = torch.from_numpy(g.v.astype(np.int32)).pin_memory()
+    obU = torch.empty(nU, dtype=torch.int64).pin_memory()
+    obV = torch.empty(nV, dtype=torch.int64).pin_memory()
+    obe = torch.empty(m, dtype=torch.int64).pin_memory()
+
+    def e2e_step():
+        hh = ctypes.c_void_p()
+        bfc._check(L.bfc_graph_from_edges(hu.data_ptr(), hv.data_ptr(), m, nU, nV, 0, sptr, ctypes.byref(hh)),
+                   "bfc_graph_from_edges")
+        h = hh.value
+        try:
+            bfc._check(L.bfc_exact(h, 0, ctypes.byref(Bh), ctypes.byref(side_h), sptr), "bfc_exact")
+            bfc._check(L.bfc_per_vertex(h, 0, bU.data_ptr(), bV.data_ptr(), None, sptr), "bfc_per_vertex")
+            bfc._check(L.bfc_per_edge(h, 0, be.data_ptr(), None, sptr), "bfc_per_edge")
+            obU.copy_(bU, non_blocking=True)
+            obV.copy_(bV, non_blocking=True)
+            obe.copy_(be, non_blocking=True)
+        finally:
+            bfc.bfc_graph_free(h)
+        torch.cuda.synchronize()
+
+    e2e_steps = max(2, min(args.steps, 5))
+    e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    barrier()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    assert int(obU.sum()) == 2 * Bval and int(obe.sum()) == 4 * Bval
+
+    # ---- roofline of the dominant kernel
+    peak, peak_kind = measured_peaks()
+    dom = max(prof, key=lambda t: prof[t][1])
+    n_launch, tot_ms = prof[dom]
+    cls = dom.split(".")[0]
+    mode = dom.split(".")[1]
+    wedges = ps["work"][cls]
+    rows = ps["rows"][cls]
+    per_wedge = 8 if mode == "edge" else 4
+    alg_bytes = per_wedge * wedges + 16 * rows
+    avg_ms = tot_ms / max(n_launch, 1)
+    achieved = alg_bytes / (avg_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": f"k_{cls}_class<{mode}>", "peak_kind": peak_kind,
+                "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "wedges/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nU": nU, "nV": nV, "m": m, "W": W, "B": Bval, "start_side": "UV"[side],
+                   "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (edge list 400 MB)",
+                   "classes": ps["count"], "class_wedges": ps["work"]},
+        "e2e": {"value": world * W / (e2e_ms / 1e3), "unit": "wedges/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": 8 * m, "d2h_bytes_per_step": 8 * (nU + nV + m) + 16},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "roofline": roofline,
+        "kernels_ms_per_step": {t: prof[t][1] / args.steps for t in prof if prof[t][0]},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        v, desc, P = oracle_sample(g, side, args.cpu_budget)
+        P.close()
+        line["cpu_baseline"] = {"value": v, "unit": "wedges/s", "cores": 1, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("own", "reference"), default="own")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_own(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

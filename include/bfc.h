@@ -161,6 +161,25 @@ int bfc_proposal_from_weights(bfc_graph *g, const uint32_t *weights, uint32_t fl
                               bfc_proposal **out);
 int bfc_proposal_free(bfc_proposal *p);
 
+/* ---- instrumentation (no counterpart in the paper) --------------------- */
+
+/* Work split of the start side `side` (0 = U, 1 = V) after its layout is
+ * built (any counting call builds it; this call builds it if needed).
+ * out[0..10] (host) = nS, then for the classes skip / warp / cta:
+ * vertex counts out[1..3], wedges walked out[4..6], start-row entries
+ * out[7..9], and out[10] = total wedges W of the midpoint side (Lemma 2). */
+int bfc_plan_stats(bfc_graph *g, int side, uint64_t *out, void *stream);
+
+/* Device timing of the library's counting kernels: when enabled, every
+ * wedge-kernel launch is bracketed by CUDA events on the launch stream.
+ * bfc_profile_read synchronises on the recorded events and returns, for the
+ * kernel tag (e.g. "cta.total", "warp.vertex", "cta.edge"), the number of
+ * launches and their summed device time in milliseconds.  Tags:
+ * {warp,cta}.{total,vertex,edge}. */
+int bfc_profile_enable(int on);
+int bfc_profile_reset(void);
+int bfc_profile_read(const char *tag, uint64_t *launches, double *total_ms);
+
 /* ---- misc -------------------------------------------------------------- */
 const char *bfc_strerror(int code);
 /* Number of kernel launches this library has made on the calling thread's

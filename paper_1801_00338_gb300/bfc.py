@@ -64,6 +64,14 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         f = getattr(L, name)
         f.argtypes = args
         f.restype = i32
+    L.bfc_plan_stats.argtypes = [P, i32, P, P]
+    L.bfc_plan_stats.restype = i32
+    L.bfc_profile_enable.argtypes = [i32]
+    L.bfc_profile_enable.restype = i32
+    L.bfc_profile_reset.argtypes = []
+    L.bfc_profile_reset.restype = i32
+    L.bfc_profile_read.argtypes = [ctypes.c_char_p, P, P]
+    L.bfc_profile_read.restype = i32
     L.bfc_strerror.argtypes = [i32]
     L.bfc_strerror.restype = ctypes.c_char_p
     L.bfc_launch_count.argtypes = []
@@ -102,6 +110,33 @@ def _dptr(t) -> int:
 
 def bfc_launch_count() -> int:
     return int(load().bfc_launch_count())
+
+
+def bfc_plan_stats(h: int, side: int, stream=None) -> dict:
+    out = np.zeros(11, np.uint64)
+    _check(load().bfc_plan_stats(h, side, out.ctypes.data, _stream_ptr(stream)), "bfc_plan_stats")
+    o = [int(x) for x in out]
+    return {"nS": o[0], "count": {"skip": o[1], "warp": o[2], "cta": o[3]},
+            "work": {"skip": o[4], "warp": o[5], "cta": o[6]},
+            "rows": {"skip": o[7], "warp": o[8], "cta": o[9]}, "W": o[10]}
+
+
+def bfc_profile_enable(on: bool = True):
+    _check(load().bfc_profile_enable(1 if on else 0), "bfc_profile_enable")
+
+
+def bfc_profile_reset():
+    _check(load().bfc_profile_reset(), "bfc_profile_reset")
+
+
+def bfc_profile_read(tag: str) -> tuple[int, float]:
+    n = ctypes.c_uint64()
+    ms = ctypes.c_double()
+    _check(load().bfc_profile_read(tag.encode(), ctypes.byref(n), ctypes.byref(ms)), "bfc_profile_read")
+    return int(n.value), float(ms.value)
+
+
+PROFILE_TAGS = [f"{c}.{m}" for c in ("warp", "cta") for m in ("total", "vertex", "edge")]
 
 
 # ----------------------------------------------------------------------------
@@ -250,6 +285,9 @@ class Graph:
 
     def per_edge(self, side=None, stream=None):
         return bfc_per_edge(self.h, self.m, _SIDE[side], stream)
+
+    def plan_stats(self, side: int, stream=None):
+        return bfc_plan_stats(self.h, side, stream)
 
     def edges(self, stream=None):
         return bfc_graph_edges(self.h, self.m, stream)

@@ -32,6 +32,11 @@ struct Status {
   } while (0)
 
 void note_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+
+// Optional event timing of kernel launches (see bfc_profile_* in bfc.h).
+bool profile_on();
+void profile_begin(const char *tag, cudaStream_t s);  // record the start event
+void profile_end(const char *tag, cudaStream_t s);    // record the end event
 void count_launch(uint64_t n = 1);
 
 // Check the launch that was just made.
@@ -119,6 +124,8 @@ struct Plan {
   DBuf cls;              // u32[nS]  ranks grouped by class
   uint32_t cls_count[4] = {0, 0, 0, 0};
   uint32_t cls_begin[4] = {0, 0, 0, 0};
+  uint64_t cls_work[3] = {0, 0, 0};   // wedges walked per class
+  uint64_t cls_rows[3] = {0, 0, 0};   // start-row entries per class
   uint64_t total_work = 0;     // sum of work = W of the midpoint side
   uint32_t max_deg_S = 0;
 };
@@ -147,7 +154,7 @@ int choose_side(const bfc_graph *g, uint32_t flags);
 int read_device_error(bfc_graph *g, cudaStream_t s);  // maps DERR_* bits to a status and clears
 
 // wedge.cu
-enum Mode { MODE_TOTAL = 0, MODE_VERTEX = 1, MODE_EDGE = 2 };
+enum Mode { MODE_TOTAL = 0, MODE_VERTEX = 1, MODE_EDGE = 2, MODE_SINGLE = 3 };
 // Counts with the start side of plan p.  out_B receives B (device u64).
 // bS / bM: per-vertex outputs of the start / midpoint side (device, original
 // ids) or null; be: per-edge output (canonical ids) or null.
@@ -155,6 +162,10 @@ int wedge_count(bfc_graph *g, Plan &p, Mode mode, unsigned long long *d_B, uint6
                 uint64_t *be, cudaStream_t s);
 int plan_classify(bfc_graph *g, Plan &p, cudaStream_t s);
 void plan_free(Plan &p, cudaStream_t s);
+// Algorithm 2 for a batch of start ranks of plan p: out[i] = b of the vertex
+// at rank item_rank[i] (every other start vertex w != v, full midpoint rows).
+int vbfc_batch(bfc_graph *g, Plan &p, const uint32_t *item_rank, uint32_t n_items, unsigned long long *out,
+               cudaStream_t s);
 // Filter plan `parent` to the canonical edges with keep[e] != 0 into `out`
 // (same start side and rank order; rows stay sorted).
 int plan_filter(bfc_graph *g, const Plan &parent, const uint32_t *keep, Plan &out, cudaStream_t s);

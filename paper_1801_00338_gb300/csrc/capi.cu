@@ -145,6 +145,21 @@ int bfc_per_edge(bfc_graph *g, uint32_t flags, uint64_t *be, uint64_t *out_B, vo
   return finish_count(g, out_B, s);
 }
 
+int bfc_plan_stats(bfc_graph *g, int side, uint64_t *out, void *stream) {
+  if (!g || !out || (side != 0 && side != 1)) return BFC_EINVAL;
+  cudaStream_t s = as_stream(stream);
+  BFC_TRY(plan_build(g, side, s));
+  const Plan &p = g->plan[side];
+  out[0] = p.nS;
+  for (int c = 0; c < 3; c++) {
+    out[1 + c] = p.cls_count[c];
+    out[4 + c] = p.cls_work[c];
+    out[7 + c] = p.cls_rows[c];
+  }
+  out[10] = p.total_work;
+  return BFC_OK;
+}
+
 const char *bfc_strerror(int code) {
   switch (code) {
     case BFC_OK: return "ok";

@@ -2,6 +2,13 @@
 // Written for sm_103a: 256-thread blocks, warp shuffles, __match_any_sync for
 // stable in-warp ranking.  Used only for graph preparation.
 #include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
 
 #include "bfc_internal.cuh"
 
@@ -18,6 +25,39 @@ void count_launch(uint64_t n) {
   __atomic_add_fetch(&g_launches, n, __ATOMIC_RELAXED);
 }
 uint64_t launches_total() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+// ---------------------------------------------------------------------------
+// kernel timing with CUDA events (enabled on request)
+// ---------------------------------------------------------------------------
+namespace {
+struct ProfEntry {
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> done;
+  cudaEvent_t open = nullptr;
+};
+std::mutex g_prof_mu;
+std::map<std::string, ProfEntry> g_prof;
+bool g_prof_on = false;
+}  // namespace
+
+bool profile_on() { return g_prof_on; }
+void profile_begin(const char *tag, cudaStream_t s) {
+  if (!g_prof_on) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  ProfEntry &e = g_prof[tag];
+  if (cudaEventCreate(&e.open) != cudaSuccess) { e.open = nullptr; return; }
+  cudaEventRecord(e.open, s);
+}
+void profile_end(const char *tag, cudaStream_t s) {
+  if (!g_prof_on) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  ProfEntry &e = g_prof[tag];
+  if (!e.open) return;
+  cudaEvent_t end;
+  if (cudaEventCreate(&end) != cudaSuccess) return;
+  cudaEventRecord(end, s);
+  e.done.emplace_back(e.open, end);
+  e.open = nullptr;
+}
 
 int dalloc(DBuf &b, size_t bytes, cudaStream_t s) {
   if (b.p && b.bytes >= bytes) return BFC_OK;
@@ -330,4 +370,45 @@ int radix_sort_u32(const uint32_t *keys_in, uint32_t *keys_out, const uint32_t *
 
 }  // namespace bfc
 
-extern "C" uint64_t bfc_launch_count(void) { return bfc::launches_total(); }
+extern "C" {
+uint64_t bfc_launch_count(void) { return bfc::launches_total(); }
+
+int bfc_profile_enable(int on) {
+  bfc::g_prof_on = on != 0;
+  return BFC_OK;
+}
+
+int bfc_profile_reset(void) {
+  std::lock_guard<std::mutex> lk(bfc::g_prof_mu);
+  for (auto &kv : bfc::g_prof) {
+    for (auto &pr : kv.second.done) {
+      cudaEventSynchronize(pr.second);
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+    if (kv.second.open) cudaEventDestroy(kv.second.open);
+  }
+  bfc::g_prof.clear();
+  return BFC_OK;
+}
+
+int bfc_profile_read(const char *tag, uint64_t *launches, double *total_ms) {
+  if (!tag) return BFC_EINVAL;
+  std::lock_guard<std::mutex> lk(bfc::g_prof_mu);
+  uint64_t n = 0;
+  double ms = 0.0;
+  auto it = bfc::g_prof.find(tag);
+  if (it != bfc::g_prof.end()) {
+    for (auto &pr : it->second.done) {
+      if (cudaEventSynchronize(pr.second) != cudaSuccess) return BFC_ECUDA;
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, pr.first, pr.second) != cudaSuccess) return BFC_ECUDA;
+      ms += t;
+      n++;
+    }
+  }
+  if (launches) *launches = n;
+  if (total_ms) *total_ms = ms;
+  return BFC_OK;
+}
+}  // extern "C"

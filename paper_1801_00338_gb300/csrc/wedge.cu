@@ -58,6 +58,9 @@ struct WArgs {
   uint32_t *seg;        // 5 u32 per segment: begin, end, cur, pstart, next
   uint32_t *seg_row;    // row index per segment
   uint32_t seg_cap;
+  // MODE_SINGLE (Algorithm 2 on a batch): list holds item ids
+  const uint32_t *item_rank;
+  unsigned long long *bitem;
 };
 
 __device__ __forceinline__ uint64_t pairs_of(uint32_t c) { return (uint64_t)c * (c - (c > 0)) / 2; }
@@ -114,15 +117,18 @@ __device__ __forceinline__ uint32_t wh_lookup(const uint32_t *keys, const uint32
 // Expand the wedges of start-row entries [rb, re) 32 rows at a time and call
 // f(i, j) for every wedge target index i (into mR) of row entry j.  All 32
 // lanes must call this together.
-template <class F>
+// FULL: the whole midpoint row (Algorithm 2: every w != v) instead of the
+// part after v.
+template <bool FULL, class F>
 __device__ __forceinline__ void warp_for_each_wedge(const WArgs &a, uint64_t rb, uint64_t re, F f) {
   const int lane = threadIdx.x & 31;
   for (uint64_t chunk = rb; chunk < re; chunk += 32) {
     uint64_t j = chunk + lane;
     uint32_t b = 0, len = 0;
     if (j < re) {
-      b = a.sB[j];
-      uint32_t e = (uint32_t)a.offM[a.sX[j] + 1];
+      const uint32_t x = a.sX[j];
+      b = FULL ? (uint32_t)a.offM[x] : a.sB[j];
+      uint32_t e = (uint32_t)a.offM[x + 1];
       len = e - b;
     }
     uint32_t incl = warp_incl_scan_u32(len);
@@ -158,15 +164,19 @@ __global__ void __launch_bounds__(WH_WARPS * 32) k_warp_class(WArgs a) {
     if (lane == 0) idx = atomicAdd(a.queue, 1u);
     idx = __shfl_sync(0xffffffffu, idx, 0);
     if (idx >= a.list_n) break;
-    const uint32_t r = a.list[idx];
+    const uint32_t item = a.list[idx];
+    const uint32_t r = (MODE == MODE_SINGLE) ? a.item_rank[item] : item;
     const uint64_t rb = a.offR[r], re = a.offR[r + 1];
-    warp_for_each_wedge(a, rb, re, [&](uint32_t i, uint64_t) { wh_insert(keys, cnts, a.mR[i]); });
+    warp_for_each_wedge<MODE == MODE_SINGLE>(a, rb, re, [&](uint32_t i, uint64_t) {
+      const uint32_t w = a.mR[i];
+      if (MODE != MODE_SINGLE || w != r) wh_insert(keys, cnts, w);
+    });
     __syncwarp();
     if (MODE != MODE_TOTAL) {
       // second sweep: every wedge learns its final multiplicity
       for (uint64_t chunk = rb; chunk < re; chunk += 32) {
         // per-row sums: accumulate into per-lane slots then flush per row
-        warp_for_each_wedge(a, chunk, min(chunk + 32, re), [&](uint32_t i, uint64_t j) {
+        warp_for_each_wedge<false>(a, chunk, min(chunk + 32, re), [&](uint32_t i, uint64_t j) {
           uint32_t c = wh_lookup(keys, cnts, a.mR[i]);
           if (c > 1) {
             if (MODE == MODE_EDGE) {
@@ -195,6 +205,7 @@ __global__ void __launch_bounds__(WH_WARPS * 32) k_warp_class(WArgs a) {
     if (lane == 0) {
       localB += acc;
       if (MODE == MODE_VERTEX && acc) atomicAdd(&a.bS[a.vert_of[r]], (unsigned long long)acc);
+      if (MODE == MODE_SINGLE) a.bitem[item] = acc;
     }
     __syncwarp();
   }
@@ -235,15 +246,17 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_class(WArgs a) {
     __syncthreads();
     const uint32_t idx = s_idx;
     if (idx >= a.list_n) break;
-    const uint32_t r = a.list[idx];
+    const uint32_t item = a.list[idx];
+    const uint32_t r = (MODE == MODE_SINGLE) ? a.item_rank[item] : item;
     const uint64_t rb = a.offR[r], re = a.offR[r + 1];
     // ---- segments: each start-row entry's suffix cut into pieces of CT_SEG
     for (uint64_t base = rb; base < re; base += CT_THREADS) {
       uint64_t j = base + threadIdx.x;
       uint32_t b = 0, e = 0, ns = 0;
       if (j < re) {
-        b = a.sB[j];
-        e = (uint32_t)a.offM[a.sX[j] + 1];
+        const uint32_t x = a.sX[j];
+        b = (MODE == MODE_SINGLE) ? (uint32_t)a.offM[x] : a.sB[j];
+        e = (uint32_t)a.offM[x + 1];
         ns = (e - b + CT_SEG - 1) / CT_SEG;
       }
       // block exclusive scan of ns
@@ -274,7 +287,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_class(WArgs a) {
     const uint32_t nseg = min(s_carry, a.seg_cap);
     // ---- walk the windows
     uint32_t lo, hi;
-    tile_bounds(a.nS, r + 1, lo, hi);
+    tile_bounds(a.nS, (MODE == MODE_SINGLE) ? 0u : r + 1, lo, hi);
     while (true) {
       // count
       for (uint32_t sidx = warp; sidx < nseg; sidx += NW) {
@@ -287,7 +300,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_class(WArgs a) {
             uint32_t w = (i < end) ? a.mR[i] : 0xFFFFFFFFu;
             bool in = w < hi;
             uint32_t bal = __ballot_sync(0xffffffffu, in);
-            if (in) atomicAdd(&ctr[w - lo], 1u);
+            if (in && (MODE != MODE_SINGLE || w != r)) atomicAdd(&ctr[w - lo], 1u);
             uint32_t n = __popc(bal);
             pos += n;
             if (n < 32) {
@@ -355,6 +368,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_class(WArgs a) {
     if (threadIdx.x == 0) {
       localB += s_acc;
       if (MODE == MODE_VERTEX && s_acc) atomicAdd(&a.bS[a.vert_of[r]], s_acc);
+      if (MODE == MODE_SINGLE) a.bitem[item] = s_acc;
     }
     __syncthreads();
   }
@@ -365,12 +379,14 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_class(WArgs a) {
 // classification
 // ---------------------------------------------------------------------------
 __global__ void k_classify(const uint64_t *offR, const uint64_t *work, uint32_t nS, uint32_t *cls_of,
-                           unsigned int *counts, unsigned long long *maxseg) {
+                           unsigned int *counts, unsigned long long *maxseg, unsigned long long *cls_sums) {
   for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nS; r += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t d = offR[r + 1] - offR[r], w = work[r];
     uint32_t c = (d < 2 || w == 0) ? CLS_SKIP : (w <= WH_MAX_WORK ? CLS_WARP : CLS_CTA);
     cls_of[r] = c;
     atomicAdd(&counts[c], 1u);
+    if (w) atomicAdd(&cls_sums[c], (unsigned long long)w);
+    if (d) atomicAdd(&cls_sums[3 + c], (unsigned long long)d);
     if (c == CLS_CTA) atomicMax(maxseg, (unsigned long long)(d + w / CT_SEG + 1));
   }
 }
@@ -410,18 +426,21 @@ int plan_classify(bfc_graph *g, Plan &p, cudaStream_t s) {
   int rc = BFC_OK;
 #define PC_TRY(x) do { rc = (x); if (rc) { cleanup(); return rc; } } while (0)
   PC_TRY(dalloc(cls_of, (uint64_t)std::max<uint32_t>(nS, 1) * 4, s));
-  PC_TRY(dalloc(cnt, 64, s));
-  BFC_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, 64, s));
+  PC_TRY(dalloc(cnt, 128, s));
+  BFC_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, 128, s));
   unsigned int *counts = ptr<unsigned int>(cnt);
   unsigned long long *maxseg = reinterpret_cast<unsigned long long *>(counts + 8);
+  unsigned long long *sums = reinterpret_cast<unsigned long long *>(counts + 16);  // 6 x u64
   k_classify<<<grid_for(nS, 256), 256, 0, s>>>(ptr<uint64_t>(p.offR), ptr<uint64_t>(p.work), nS,
-                                              ptr<uint32_t>(cls_of), counts, maxseg);
+                                              ptr<uint32_t>(cls_of), counts, maxseg, sums);
   count_launch();
   unsigned int hc[8];
-  unsigned long long hmax = 0;
+  unsigned long long hmax = 0, hs[6];
   BFC_CUDA_TRY(cudaMemcpyAsync(hc, counts, 32, cudaMemcpyDeviceToHost, s));
   BFC_CUDA_TRY(cudaMemcpyAsync(&hmax, maxseg, 8, cudaMemcpyDeviceToHost, s));
+  BFC_CUDA_TRY(cudaMemcpyAsync(hs, sums, 48, cudaMemcpyDeviceToHost, s));
   BFC_CUDA_TRY(cudaStreamSynchronize(s));
+  for (int c = 0; c < 3; c++) { p.cls_work[c] = hs[c]; p.cls_rows[c] = hs[3 + c]; }
   unsigned int hb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int c = 0; c < 3; c++) {
     p.cls_count[c] = hc[c];
@@ -467,16 +486,22 @@ static int sm_count() {
   return n;
 }
 
+static const char *tag_of(int cls, int mode) {
+  static const char *tags[2][3] = {{"warp.total", "warp.vertex", "warp.edge"}, {"cta.total", "cta.vertex", "cta.edge"}};
+  return tags[cls == CLS_CTA ? 1 : 0][mode];
+}
+
 template <int MODE>
-static int launch_classes(bfc_graph *g, Plan &p, WArgs a, cudaStream_t s) {
+static int launch_lists(bfc_graph *g, WArgs a, const uint32_t *warp_list, uint32_t n_warp, const uint32_t *cta_list,
+                        uint32_t n_cta, uint32_t seg_cap, cudaStream_t s) {
   const int sms = sm_count();
   unsigned int *queues = ptr<unsigned int>(g->acc) + 16;  // two counters
   BFC_CUDA_TRY(cudaMemsetAsync(queues, 0, 8, s));
-  // warp class
-  if (p.cls_count[CLS_WARP]) {
+  const int tmode = MODE == MODE_SINGLE ? 0 : MODE;
+  if (n_warp) {
     WArgs w = a;
-    w.list = ptr<uint32_t>(p.cls) + p.cls_begin[CLS_WARP];
-    w.list_n = p.cls_count[CLS_WARP];
+    w.list = warp_list;
+    w.list_n = n_warp;
     w.queue = queues;
     const size_t smem = (size_t)WH_WARPS * 2 * WH_SLOTS * 4;
     BFC_CUDA_TRY(cudaFuncSetAttribute(k_warp_class<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -484,30 +509,40 @@ static int launch_classes(bfc_graph *g, Plan &p, WArgs a, cudaStream_t s) {
     BFC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_warp_class<MODE>, WH_WARPS * 32, smem));
     unsigned grid = (unsigned)std::max(1, occ) * sms;
     grid = std::min<unsigned>(grid, (w.list_n + WH_WARPS - 1) / WH_WARPS);
+    profile_begin(tag_of(CLS_WARP, tmode), s);
     k_warp_class<MODE><<<grid, WH_WARPS * 32, smem, s>>>(w);
     BFC_LAUNCHED();
+    profile_end(tag_of(CLS_WARP, tmode), s);
   }
-  if (p.cls_count[CLS_CTA]) {
+  if (n_cta) {
     WArgs c = a;
-    c.list = ptr<uint32_t>(p.cls) + p.cls_begin[CLS_CTA];
-    c.list_n = p.cls_count[CLS_CTA];
+    c.list = cta_list;
+    c.list_n = n_cta;
     c.queue = queues + 1;
     const size_t smem = (size_t)CT_Z * 4;
     BFC_CUDA_TRY(cudaFuncSetAttribute(k_cta_class<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     unsigned grid = std::min<unsigned>((unsigned)sms, c.list_n);
-    c.seg_cap = std::max<uint32_t>(p.cls_count[3], 1);
+    c.seg_cap = std::max<uint32_t>(seg_cap, 1);
     const uint64_t need = (uint64_t)grid * c.seg_cap * 6 * 4;
     BFC_TRY(g->scr.reserve(need, s));
     c.seg = static_cast<uint32_t *>(g->scr.base());
     c.seg_row = c.seg + (uint64_t)grid * c.seg_cap * 5;
+    profile_begin(tag_of(CLS_CTA, tmode), s);
     k_cta_class<MODE><<<grid, CT_THREADS, smem, s>>>(c);
     BFC_LAUNCHED();
+    profile_end(tag_of(CLS_CTA, tmode), s);
   }
   return BFC_OK;
 }
 
-int wedge_count(bfc_graph *g, Plan &p, Mode mode, unsigned long long *d_B, uint64_t *bS, uint64_t *bM, uint64_t *be,
-                cudaStream_t s) {
+template <int MODE>
+static int launch_classes(bfc_graph *g, Plan &p, WArgs a, cudaStream_t s) {
+  const uint32_t *cls = ptr<uint32_t>(p.cls);
+  return launch_lists<MODE>(g, a, cls + p.cls_begin[CLS_WARP], p.cls_count[CLS_WARP], cls + p.cls_begin[CLS_CTA],
+                            p.cls_count[CLS_CTA], p.cls_count[3], s);
+}
+
+static WArgs args_of(bfc_graph *g, Plan &p) {
   WArgs a{};
   a.nS = p.nS;
   a.offR = ptr<uint64_t>(p.offR);
@@ -518,11 +553,95 @@ int wedge_count(bfc_graph *g, Plan &p, Mode mode, unsigned long long *d_B, uint6
   a.mR = ptr<uint32_t>(p.mR);
   a.mEid = ptr<uint32_t>(p.mEid);
   a.vert_of = ptr<uint32_t>(p.vert_of);
+  a.err = ptr<uint32_t>(g->err);
+  return a;
+}
+
+// ---------------------------------------------------------------------------
+// batched Algorithm 2
+// ---------------------------------------------------------------------------
+__global__ void k_item_classify(const uint32_t *item_rank, uint32_t n, const uint64_t *offR, const uint32_t *sX,
+                                const uint64_t *offM, uint32_t *cls_of, unsigned int *counts,
+                                unsigned long long *maxseg, unsigned long long *out) {
+  const int lane = threadIdx.x & 31;
+  uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t i = warp; i < n; i += nw) {
+    const uint32_t r = item_rank[i];
+    const uint64_t b = offR[r], e = offR[r + 1];
+    uint64_t w = 0;
+    for (uint64_t j = b + lane; j < e; j += 32) {
+      const uint32_t x = sX[j];
+      w += offM[x + 1] - offM[x] - 1;
+    }
+    w = warp_sum_u64(w);
+    if (lane == 0) {
+      const uint64_t d = e - b;
+      uint32_t c = (d < 2 || w == 0) ? CLS_SKIP : (w <= WH_MAX_WORK ? CLS_WARP : CLS_CTA);
+      cls_of[i] = c;
+      atomicAdd(&counts[c], 1u);
+      out[i] = 0;
+      if (c == CLS_CTA) atomicMax(maxseg, (unsigned long long)(d + w / CT_SEG + 1));
+    }
+  }
+}
+__global__ void k_item_scatter(const uint32_t *cls_of, uint32_t n, unsigned int *cursor, uint32_t *warp_list,
+                               uint32_t *cta_list) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t c = cls_of[i];
+    if (c == CLS_WARP) warp_list[atomicAdd(&cursor[0], 1u)] = (uint32_t)i;
+    else if (c == CLS_CTA) cta_list[atomicAdd(&cursor[1], 1u)] = (uint32_t)i;
+  }
+}
+
+int vbfc_batch(bfc_graph *g, Plan &p, const uint32_t *item_rank, uint32_t n_items, unsigned long long *out,
+               cudaStream_t s) {
+  if (n_items == 0) return BFC_OK;
+  DBuf cls_of, lists, cnt;
+  auto cleanup = [&]() { dfree(cls_of, s); dfree(lists, s); dfree(cnt, s); };
+  int rc = BFC_OK;
+#define VB_TRY(x) do { rc = (x); if (rc) { cleanup(); return rc; } } while (0)
+  VB_TRY(dalloc(cls_of, (uint64_t)n_items * 4, s));
+  VB_TRY(dalloc(lists, (uint64_t)n_items * 8, s));
+  VB_TRY(dalloc(cnt, 64, s));
+  BFC_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, 64, s));
+  unsigned int *counts = ptr<unsigned int>(cnt);
+  unsigned long long *maxseg = reinterpret_cast<unsigned long long *>(counts + 4);
+  k_item_classify<<<grid_for((uint64_t)n_items * 32, 256), 256, 0, s>>>(item_rank, n_items, ptr<uint64_t>(p.offR),
+                                                                        ptr<uint32_t>(p.sX), p.offM,
+                                                                        ptr<uint32_t>(cls_of), counts, maxseg, out);
+  count_launch();
+  unsigned int hc[4];
+  unsigned long long hmax = 0;
+  BFC_CUDA_TRY(cudaMemcpyAsync(hc, counts, 16, cudaMemcpyDeviceToHost, s));
+  BFC_CUDA_TRY(cudaMemcpyAsync(&hmax, maxseg, 8, cudaMemcpyDeviceToHost, s));
+  BFC_CUDA_TRY(cudaStreamSynchronize(s));
+  uint32_t *warp_list = ptr<uint32_t>(lists);
+  uint32_t *cta_list = warp_list + n_items;
+  BFC_CUDA_TRY(cudaMemsetAsync(counts + 8, 0, 8, s));
+  k_item_scatter<<<grid_for(n_items, 256), 256, 0, s>>>(ptr<uint32_t>(cls_of), n_items, counts + 8, warp_list,
+                                                       cta_list);
+  count_launch();
+  WArgs a = args_of(g, p);
+  a.item_rank = item_rank;
+  a.bitem = out;
+  unsigned long long dummyB_off = 0;
+  (void)dummyB_off;
+  a.B = ptr<unsigned long long>(g->acc) + 1;  // not read back
+  VB_TRY(launch_lists<MODE_SINGLE>(g, a, warp_list, hc[CLS_WARP], cta_list, hc[CLS_CTA],
+                                   (uint32_t)std::min<unsigned long long>(hmax, 0xFFFFFFFFull), s));
+  cleanup();
+#undef VB_TRY
+  return BFC_OK;
+}
+
+int wedge_count(bfc_graph *g, Plan &p, Mode mode, unsigned long long *d_B, uint64_t *bS, uint64_t *bM, uint64_t *be,
+                cudaStream_t s) {
+  WArgs a = args_of(g, p);
   a.B = d_B;
   a.bS = reinterpret_cast<unsigned long long *>(bS);
   a.bM = reinterpret_cast<unsigned long long *>(bM);
   a.be = reinterpret_cast<unsigned long long *>(be);
-  a.err = ptr<uint32_t>(g->err);
   switch (mode) {
     case MODE_TOTAL: return launch_classes<MODE_TOTAL>(g, p, a, s);
     case MODE_VERTEX: return launch_classes<MODE_VERTEX>(g, p, a, s);

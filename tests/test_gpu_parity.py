@@ -182,3 +182,39 @@ def test_clrspar_trials_match_oracle(bfc):
         ob, oe = O.clrspar_trial(g.u, g.v, g.nU, g.nV, 3, 99, t)
         assert int(beta[t]) == ob
         assert est[t] == oe
+
+
+def _vsamp_check(bfc, g, k, trials, seed, weights=None):
+    import torch
+    with bfc.Graph(g.u, g.v, g.nU, g.nV) as G:
+        prop = bfc.bfc_proposal_from_weights(G.h, weights) if weights is not None else None
+        try:
+            est, drawn, bd = G.vsamp(k, trials, seed, proposal=prop, want_draws=True)
+        finally:
+            if prop:
+                bfc.bfc_proposal_free(prop)
+        drawn = u64(drawn).reshape(trials, k)
+        bd = u64(bd).reshape(trials, k)
+    for t in range(trials):
+        oe, od, ob = O.vsamp_trial(g.u, g.v, g.nU, g.nV, k, seed, t, weights=weights)
+        assert np.array_equal(drawn[t], od)
+        assert np.array_equal(bd[t], ob)
+        assert est[t] == pytest.approx(oe, rel=1e-12, abs=0.0)
+
+
+def test_vsamp_uniform_matches_oracle(bfc):
+    g = synth.chung_lu_scaled(3000, 9000, 40_000, 2.1, 2.4, 5)
+    _vsamp_check(bfc, g, 300, 4, 77)
+
+
+def test_vsamp_weighted_matches_oracle(bfc):
+    g = synth.chung_lu_scaled(3000, 9000, 40_000, 2.1, 2.4, 6)
+    n = g.nU + g.nV
+    w = (synth.splitmix64(9, 0, n) >> np.uint64(44)).astype(np.uint32)
+    _vsamp_check(bfc, g, 500, 3, 5, weights=w)
+
+
+def test_vsamp_on_multi_window_graph(bfc):
+    """Draws that land on CTA-class vertices walk every rank window (whole midpoint rows)."""
+    g = synth.chung_lu_scaled(120_000, 30_000, 600_000, 2.1, 2.5, 31)
+    _vsamp_check(bfc, g, 64, 2, 3)
