@@ -284,14 +284,14 @@ def run_own(args, rank, world, local_rank):
     n_launch, tot_ms = prof[dom]
     cls = dom.split(".")[0]
     mode = dom.split(".")[1]
-    wedges = ps["work"][cls]
-    rows = ps["rows"][cls]
+    wedges = sum(ps["work"][c] for c in bfc.TAG_CLASSES[cls])
+    rows = sum(ps["rows"][c] for c in bfc.TAG_CLASSES[cls])
     per_wedge = 8 if mode == "edge" else 4
     alg_bytes = per_wedge * wedges + 16 * rows
     avg_ms = tot_ms / max(n_launch, 1)
     achieved = alg_bytes / (avg_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": f"k_{cls}_class<{mode}>", "peak_kind": peak_kind,
+                "traffic": None, "kernel": {"warp": "k_warp_class", "win": "k_cta_win", "big": "k_cta_big"}[cls] + f"<{mode}>", "peak_kind": peak_kind,
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms}
 
     line = {

@@ -165,17 +165,18 @@ int bfc_proposal_free(bfc_proposal *p);
 
 /* Work split of the start side `side` (0 = U, 1 = V) after its layout is
  * built (any counting call builds it; this call builds it if needed).
- * out[0..10] (host) = nS, then for the classes skip / warp / cta:
- * vertex counts out[1..3], wedges walked out[4..6], start-row entries
- * out[7..9], and out[10] = total wedges W of the midpoint side (Lemma 2). */
+ * out (host, 20 entries): out[0] = nS; then for the six kernel classes
+ * skip / warp / win8 / win16 / win32 / big: vertex counts out[1..6], wedges
+ * walked out[7..12], start-row entries out[13..18]; out[19] = total wedges W
+ * of the midpoint side (Lemma 2). */
 int bfc_plan_stats(bfc_graph *g, int side, uint64_t *out, void *stream);
 
 /* Device timing of the library's counting kernels: when enabled, every
  * wedge-kernel launch is bracketed by CUDA events on the launch stream.
  * bfc_profile_read synchronises on the recorded events and returns, for the
- * kernel tag (e.g. "cta.total", "warp.vertex", "cta.edge"), the number of
+ * kernel tag (e.g. "win.total", "warp.vertex", "big.edge"), the number of
  * launches and their summed device time in milliseconds.  Tags:
- * {warp,cta}.{total,vertex,edge}. */
+ * {warp,win,big}.{total,vertex,edge,single}. */
 int bfc_profile_enable(int on);
 int bfc_profile_reset(void);
 int bfc_profile_read(const char *tag, uint64_t *launches, double *total_ms);

@@ -112,13 +112,17 @@ def bfc_launch_count() -> int:
     return int(load().bfc_launch_count())
 
 
+CLASSES = ("skip", "warp", "win8", "win16", "win32", "big")
+
+
 def bfc_plan_stats(h: int, side: int, stream=None) -> dict:
-    out = np.zeros(11, np.uint64)
+    """Per-class vertex counts, wedges and start-row entries of a start side's layout."""
+    out = np.zeros(20, np.uint64)
     _check(load().bfc_plan_stats(h, side, out.ctypes.data, _stream_ptr(stream)), "bfc_plan_stats")
     o = [int(x) for x in out]
-    return {"nS": o[0], "count": {"skip": o[1], "warp": o[2], "cta": o[3]},
-            "work": {"skip": o[4], "warp": o[5], "cta": o[6]},
-            "rows": {"skip": o[7], "warp": o[8], "cta": o[9]}, "W": o[10]}
+    n = len(CLASSES)
+    return {"nS": o[0], "count": dict(zip(CLASSES, o[1:1 + n])), "work": dict(zip(CLASSES, o[1 + n:1 + 2 * n])),
+            "rows": dict(zip(CLASSES, o[1 + 2 * n:1 + 3 * n])), "W": o[1 + 3 * n]}
 
 
 def bfc_profile_enable(on: bool = True):
@@ -136,7 +140,9 @@ def bfc_profile_read(tag: str) -> tuple[int, float]:
     return int(n.value), float(ms.value)
 
 
-PROFILE_TAGS = [f"{c}.{m}" for c in ("warp", "cta") for m in ("total", "vertex", "edge")]
+PROFILE_TAGS = [f"{c}.{m}" for c in ("warp", "win", "big") for m in ("total", "vertex", "edge", "single")]
+# kernel tag -> the classes it runs
+TAG_CLASSES = {"warp": ("warp",), "win": ("win8", "win16", "win32"), "big": ("big",)}
 
 
 # ----------------------------------------------------------------------------

@@ -122,10 +122,12 @@ struct Plan {
   DBuf work;             // u64[nS]  ordered wedges walked from each start rank
   // vertex classes (ranks), see wedge.cu
   DBuf cls;              // u32[nS]  ranks grouped by class
-  uint32_t cls_count[4] = {0, 0, 0, 0};
-  uint32_t cls_begin[4] = {0, 0, 0, 0};
-  uint64_t cls_work[3] = {0, 0, 0};   // wedges walked per class
-  uint64_t cls_rows[3] = {0, 0, 0};   // start-row entries per class
+  static constexpr int NCLS = 6;      // skip, warp, win8, win16, win32, big (wedge.cu)
+  uint32_t cls_count[NCLS] = {};
+  uint32_t cls_begin[NCLS] = {};
+  uint64_t cls_work[NCLS] = {};       // wedges walked per class
+  uint64_t cls_rows[NCLS] = {};       // start-row entries per class
+  uint32_t big_seg_cap = 0;           // segment capacity of the big class
   uint64_t total_work = 0;     // sum of work = W of the midpoint side
   uint32_t max_deg_S = 0;
 };

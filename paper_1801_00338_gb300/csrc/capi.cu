@@ -151,12 +151,12 @@ int bfc_plan_stats(bfc_graph *g, int side, uint64_t *out, void *stream) {
   BFC_TRY(plan_build(g, side, s));
   const Plan &p = g->plan[side];
   out[0] = p.nS;
-  for (int c = 0; c < 3; c++) {
+  for (int c = 0; c < Plan::NCLS; c++) {
     out[1 + c] = p.cls_count[c];
-    out[4 + c] = p.cls_work[c];
-    out[7 + c] = p.cls_rows[c];
+    out[1 + Plan::NCLS + c] = p.cls_work[c];
+    out[1 + 2 * Plan::NCLS + c] = p.cls_rows[c];
   }
-  out[10] = p.total_work;
+  out[1 + 3 * Plan::NCLS] = p.total_work;
   return BFC_OK;
 }
 

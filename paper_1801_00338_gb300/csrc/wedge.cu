@@ -7,15 +7,25 @@
 // the number of butterflies with v and w as their start-side pair (Lemma 1,
 // Eq. (2)-(3)); every unordered pair is seen once, from its lower rank.
 //
-// Start vertices are split into classes by the number of wedges they walk
-// (Lemma 3: vBFC costs O(|Gamma^2_v|)):
-//   skip  : degree < 2 or nothing after it; c <= 1 everywhere, contributes 0
-//   warp  : few wedges; one warp per vertex, open-addressing table in shared memory
-//   cta   : many wedges; one CTA per vertex, a dense counter array in shared
-//           memory covering a window ("tile") of Z consecutive ranks; the rank
-//           space is walked tile by tile from r+1 upwards, skipping empty tiles.
+// Start vertices are split into classes by the wedges they walk (Lemma 3:
+// vBFC costs O(|Gamma^2_v|)) and by their degree (which bounds every c(v, w)):
+//   skip   degree < 2 or nothing after it: every c <= 1, contributes 0
+//   warp   <= 512 wedges: one warp per vertex, open addressing in shared memory
+//   win8   degree <= 255: one CTA per vertex, dense 8-bit counters in shared
+//          memory over a window of 196,608 consecutive ranks
+//   win16  degree <= 65,535: the same with 16-bit counters (98,304 ranks)
+//   win32  the same with 32-bit counters (49,152 ranks)
+//   big    more wedge-list segments than shared memory holds: the window kernel
+//          with its segment cursors in global memory
+// A window kernel walks the ranks after r window by window; a window starts at
+// the lowest rank still pending in any of the vertex's (rank-sorted) wedge
+// lists, so empty rank ranges cost nothing.  Each window has a count sweep
+// (shared-memory atomic increments) and an exchange sweep that reads C(c, 2)
+// once per distinct w and clears the counters: by re-walking the window's
+// wedges when they are few, or by scanning the counter words when they are many.
 //
-// Modes: TOTAL (B only), VERTEX (b for both sides), EDGE (b_e).
+// Modes: TOTAL (B only), VERTEX (b for both sides), EDGE (b_e), SINGLE
+// (Algorithm 2 on a batch of vertices: every w != v, whole midpoint rows).
 //   start side  b_v += sum_w C(c(v,w), 2), b_w += C(c(v,w), 2)
 //   mid side    b_x += c(v,w) - 1 for each wedge v - x - w (pairs through x)
 //   edges       b_(v,x) += c(v,w) - 1, b_(w,x) += c(v,w) - 1 for each wedge v - x - w
@@ -30,16 +40,23 @@
 namespace bfc {
 
 constexpr uint32_t EMPTY_KEY = 0xFFFFFFFFu;
-constexpr uint32_t CLS_SKIP = 0, CLS_WARP = 1, CLS_CTA = 2;
+constexpr uint32_t INF_RANK = 0xFFFFFFFFu;
+enum Cls : uint32_t { CLS_SKIP = 0, CLS_WARP = 1, CLS_W8 = 2, CLS_W16 = 3, CLS_W32 = 4, CLS_BIG = 5 };
 
 // warp class
 constexpr int WH_WARPS = 8;
 constexpr int WH_SLOTS = 1024;                    // per warp
 constexpr uint64_t WH_MAX_WORK = WH_SLOTS / 2;    // load factor <= 1/2
-// cta class
+// window classes
 constexpr int CT_THREADS = 1024;
-constexpr uint32_t CT_Z = 48 * 1024;              // u32 counters (192 KB)
-constexpr uint32_t CT_SEG = 256;                  // elements per segment
+constexpr uint32_t CT_WORDS = 48 * 1024;          // 192 KB of counter words
+constexpr uint32_t SEG = 1024;                    // wedge-list segment (elements)
+constexpr uint32_t SMAX = 1536;                   // segments held in shared memory
+constexpr uint32_t DENSE_MIN = CT_WORDS / 2;      // window wedges above which the exchange scans words
+constexpr size_t WIN_SMEM = (size_t)CT_WORDS * 4 + (size_t)SMAX * 5 * 4;
+// big class (segment cursors in global memory)
+constexpr uint32_t BIG_SEG = 256;
+constexpr uint32_t BIG_Z = CT_WORDS;
 
 struct WArgs {
   uint32_t nS;
@@ -54,7 +71,7 @@ struct WArgs {
   unsigned long long *B;
   unsigned long long *bS, *bM, *be;
   uint32_t *err;
-  // cta-class segment scratch (per CTA, seg_cap entries each)
+  // big class: segment scratch (per CTA, seg_cap entries each)
   uint32_t *seg;        // 5 u32 per segment: begin, end, cur, pstart, next
   uint32_t *seg_row;    // row index per segment
   uint32_t seg_cap;
@@ -63,6 +80,7 @@ struct WArgs {
   unsigned long long *bitem;
 };
 
+__device__ __forceinline__ uint64_t umin64(uint64_t x, uint64_t y) { return x < y ? x : y; }
 __device__ __forceinline__ uint64_t pairs_of(uint32_t c) { return (uint64_t)c * (c - (c > 0)) / 2; }
 
 __device__ __forceinline__ uint32_t warp_incl_scan_u32(uint32_t x) {
@@ -78,11 +96,6 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
   return x;  // valid in lane 0
-}
-__device__ __forceinline__ long long warp_sum_i64(long long x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-  return x;
 }
 
 // ---------------------------------------------------------------------------
@@ -116,9 +129,8 @@ __device__ __forceinline__ uint32_t wh_lookup(const uint32_t *keys, const uint32
 
 // Expand the wedges of start-row entries [rb, re) 32 rows at a time and call
 // f(i, j) for every wedge target index i (into mR) of row entry j.  All 32
-// lanes must call this together.
-// FULL: the whole midpoint row (Algorithm 2: every w != v) instead of the
-// part after v.
+// lanes must call this together.  FULL: the whole midpoint row (Algorithm 2:
+// every w != v) instead of the part after v.
 template <bool FULL, class F>
 __device__ __forceinline__ void warp_for_each_wedge(const WArgs &a, uint64_t rb, uint64_t re, F f) {
   const int lane = threadIdx.x & 31;
@@ -172,22 +184,19 @@ __global__ void __launch_bounds__(WH_WARPS * 32) k_warp_class(WArgs a) {
       if (MODE != MODE_SINGLE || w != r) wh_insert(keys, cnts, w);
     });
     __syncwarp();
-    if (MODE != MODE_TOTAL) {
+    if (MODE == MODE_VERTEX || MODE == MODE_EDGE) {
       // second sweep: every wedge learns its final multiplicity
-      for (uint64_t chunk = rb; chunk < re; chunk += 32) {
-        // per-row sums: accumulate into per-lane slots then flush per row
-        warp_for_each_wedge<false>(a, chunk, min(chunk + 32, re), [&](uint32_t i, uint64_t j) {
-          uint32_t c = wh_lookup(keys, cnts, a.mR[i]);
-          if (c > 1) {
-            if (MODE == MODE_EDGE) {
-              atomicAdd(&a.be[a.mEid[i]], (unsigned long long)(c - 1));
-              atomicAdd(&a.be[a.sEid[j]], (unsigned long long)(c - 1));
-            } else {
-              atomicAdd(&a.bM[a.sX[j]], (unsigned long long)(c - 1));
-            }
+      warp_for_each_wedge<false>(a, rb, re, [&](uint32_t i, uint64_t j) {
+        uint32_t c = wh_lookup(keys, cnts, a.mR[i]);
+        if (c > 1) {
+          if (MODE == MODE_EDGE) {
+            atomicAdd(&a.be[a.mEid[i]], (unsigned long long)(c - 1));
+            atomicAdd(&a.be[a.sEid[j]], (unsigned long long)(c - 1));
+          } else {
+            atomicAdd(&a.bM[a.sX[j]], (unsigned long long)(c - 1));
           }
-        });
-      }
+        }
+      });
       __syncwarp();
     }
     uint64_t acc = 0;
@@ -213,35 +222,252 @@ __global__ void __launch_bounds__(WH_WARPS * 32) k_warp_class(WArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// cta class: dense counters over a window of CT_Z ranks
+// window classes: packed dense counters in shared memory
 // ---------------------------------------------------------------------------
-// tile of rank w: windows are aligned to the top of the rank space,
-// window k covers [nS - (k+1) Z, nS - k Z)
-__device__ __forceinline__ void tile_bounds(uint32_t nS, uint32_t w, uint32_t &lo, uint32_t &hi) {
-  uint32_t k = (nS - 1 - w) / CT_Z;
-  hi = nS - k * CT_Z;
-  lo = hi > CT_Z ? hi - CT_Z : 0;
+// Counter of window offset idx: word idx mod CT_WORDS, field idx / CT_WORDS,
+// so consecutive ranks (a sorted wedge list) fall in consecutive words and
+// different banks.  A CW-bit field cannot overflow because every c(v, w) is at
+// most the degree of v, which the class bounds by 2^CW - 1.
+template <int CW>
+struct Ctr {
+  static constexpr uint32_t PER = 32 / CW;
+  static constexpr uint32_t MASK = (CW == 32) ? 0xFFFFFFFFu : ((1u << CW) - 1u);
+  static constexpr uint32_t Z = CT_WORDS * PER;
+  __device__ static __forceinline__ void at(uint32_t idx, uint32_t &wi, uint32_t &sh) {
+    const uint32_t q = (PER == 1) ? 0u : idx / CT_WORDS;
+    wi = idx - q * CT_WORDS;
+    sh = q * CW;
+  }
+  __device__ static __forceinline__ void inc(uint32_t *c, uint32_t idx) {
+    uint32_t wi, sh;
+    at(idx, wi, sh);
+    atomicAdd(&c[wi], 1u << sh);
+  }
+  __device__ static __forceinline__ uint32_t take(uint32_t *c, uint32_t idx) {
+    uint32_t wi, sh;
+    at(idx, wi, sh);
+    return (atomicAnd(&c[wi], ~(MASK << sh)) >> sh) & MASK;
+  }
+  __device__ static __forceinline__ uint32_t peek(const uint32_t *c, uint32_t idx) {
+    uint32_t wi, sh;
+    at(idx, wi, sh);
+    return (c[wi] >> sh) & MASK;
+  }
+};
+
+// Count the wedge targets of one segment that fall in [lo, hi), starting at
+// cur; four 32-element loads in flight per warp.  Targets are ascending, so the
+// in-window ones are a prefix.  On return cur is the first target >= hi (or
+// end) and nx that target's rank (INF_RANK at the end of the segment).
+template <int MODE, int CW>
+__device__ __forceinline__ void count_segment(const uint32_t *__restrict__ mR, uint32_t &cur, uint32_t end,
+                                              uint32_t lo, uint32_t hi, uint32_t r, uint32_t *ctr, uint32_t &nx) {
+  const int lane = threadIdx.x & 31;
+  while (true) {
+    uint32_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const uint32_t i = cur + k * 32 + lane;
+      w[k] = (i < end) ? __ldg(&mR[i]) : INF_RANK;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const bool in = w[k] < hi;
+      const uint32_t bal = __ballot_sync(0xffffffffu, in);
+      if (in && (MODE != MODE_SINGLE || w[k] != r)) Ctr<CW>::inc(ctr, w[k] - lo);
+      const uint32_t n = __popc(bal);
+      cur += n;
+      if (n < 32) {
+        const uint32_t first_out = __shfl_sync(0xffffffffu, w[k], n & 31);
+        nx = (cur < end) ? first_out : INF_RANK;
+        return;
+      }
+    }
+  }
 }
 
+template <int MODE, int CW>
+__global__ void __launch_bounds__(CT_THREADS, 1) k_cta_win(WArgs a) {
+  extern __shared__ uint32_t sm[];
+  uint32_t *ctr = sm;
+  uint32_t *s_cur = sm + CT_WORDS, *s_end = s_cur + SMAX, *s_ps = s_end + SMAX, *s_nx = s_ps + SMAX;
+  uint32_t *s_row = s_nx + SMAX;
+  __shared__ uint32_t sh_idx, sh_min, sh_carry;
+  __shared__ unsigned long long sh_acc, sh_win;
+  __shared__ uint32_t wtot[32];
+  constexpr int NW = CT_THREADS / 32;
+  constexpr uint32_t Z = Ctr<CW>::Z;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint32_t i = threadIdx.x; i < CT_WORDS; i += CT_THREADS) ctr[i] = 0;
+  uint64_t localB = 0;
+  __syncthreads();
+  while (true) {
+    if (threadIdx.x == 0) {
+      sh_idx = atomicAdd(a.queue, 1u);
+      sh_carry = 0;
+      sh_acc = 0;
+    }
+    __syncthreads();
+    const uint32_t idx = sh_idx;
+    if (idx >= a.list_n) break;
+    const uint32_t item = a.list[idx];
+    const uint32_t r = (MODE == MODE_SINGLE) ? a.item_rank[item] : item;
+    const uint64_t rb = a.offR[r], re = a.offR[r + 1];
+    // ---- segments of the vertex's wedge lists
+    for (uint64_t base = rb; base < re; base += CT_THREADS) {
+      const uint64_t j = base + threadIdx.x;
+      uint32_t b = 0, e = 0, ns = 0;
+      if (j < re) {
+        const uint32_t x = a.sX[j];
+        b = (MODE == MODE_SINGLE) ? (uint32_t)a.offM[x] : a.sB[j];
+        e = (uint32_t)a.offM[x + 1];
+        ns = (e - b + SEG - 1) / SEG;
+      }
+      const uint32_t incl = warp_incl_scan_u32(ns);
+      if (lane == 31) wtot[warp] = incl;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        uint32_t run = sh_carry;
+        for (int w = 0; w < NW; w++) { const uint32_t t = wtot[w]; wtot[w] = run; run += t; }
+        sh_carry = run;
+      }
+      __syncthreads();
+      const uint32_t first = wtot[warp] + incl - ns;
+      for (uint32_t k = 0; k < ns; k++) {
+        const uint32_t s = first + k;
+        if (s >= SMAX) { atomicOr(a.err, DERR_CAPACITY); break; }
+        const uint32_t sb = b + k * SEG;
+        s_cur[s] = sb;
+        s_end[s] = min(e, sb + SEG);
+        s_ps[s] = sb;
+        s_nx[s] = 0;  // unknown: load it
+        s_row[s] = (uint32_t)(j - rb);
+      }
+      __syncthreads();
+    }
+    const uint32_t nseg = min(sh_carry, SMAX);
+    uint32_t lo = (MODE == MODE_SINGLE) ? 0u : r + 1;
+    uint32_t hi = (uint32_t)umin64((uint64_t)a.nS, (uint64_t)lo + Z);
+    while (true) {
+      if (threadIdx.x == 0) {
+        sh_min = INF_RANK;
+        sh_win = 0;
+      }
+      __syncthreads();
+      // ---- count
+      uint32_t wcount = 0;
+      for (uint32_t s = warp; s < nseg; s += NW) {
+        uint32_t cur = s_cur[s], nx = s_nx[s];
+        const uint32_t end = s_end[s], ps = cur;
+        if (cur < end && nx < hi) count_segment<MODE, CW>(a.mR, cur, end, lo, hi, r, ctr, nx);
+        else if (cur >= end) nx = INF_RANK;
+        if (lane == 0) {
+          s_cur[s] = cur;
+          s_ps[s] = ps;
+          s_nx[s] = nx;
+          if (nx != INF_RANK) atomicMin(&sh_min, nx);
+        }
+        wcount += cur - ps;
+      }
+      if (lane == 0 && wcount) atomicAdd(&sh_win, (unsigned long long)wcount);
+      __syncthreads();
+      const uint64_t win = sh_win;
+      // ---- VERTEX / EDGE: every wedge of the window reads its final count
+      if ((MODE == MODE_VERTEX || MODE == MODE_EDGE) && win) {
+        for (uint32_t s = warp; s < nseg; s += NW) {
+          const uint32_t ps = s_ps[s], pe = s_cur[s];
+          if (ps >= pe) continue;
+          uint64_t rowsum = 0;
+          for (uint32_t i = ps + lane; i < pe; i += 32) {
+            const uint32_t c = Ctr<CW>::peek(ctr, a.mR[i] - lo);
+            if (c > 1) {
+              rowsum += c - 1;
+              if (MODE == MODE_EDGE) atomicAdd(&a.be[a.mEid[i]], (unsigned long long)(c - 1));
+            }
+          }
+          rowsum = warp_sum_u64(rowsum);
+          if (lane == 0 && rowsum) {
+            const uint64_t j = rb + s_row[s];
+            if (MODE == MODE_EDGE) atomicAdd(&a.be[a.sEid[j]], (unsigned long long)rowsum);
+            else atomicAdd(&a.bM[a.sX[j]], (unsigned long long)rowsum);
+          }
+        }
+        __syncthreads();
+      }
+      // ---- exchange: C(c, 2) once per distinct w, and clear
+      uint64_t acc = 0;
+      if (win >= DENSE_MIN) {
+        for (uint32_t wi = threadIdx.x; wi < CT_WORDS; wi += CT_THREADS) {
+          const uint32_t word = ctr[wi];
+          if (!word) continue;
+#pragma unroll
+          for (uint32_t q = 0; q < Ctr<CW>::PER; q++) {
+            const uint32_t c = (word >> (q * CW)) & Ctr<CW>::MASK;
+            if (c > 1) {
+              const uint64_t p = pairs_of(c);
+              acc += p;
+              if (MODE == MODE_VERTEX) atomicAdd(&a.bS[a.vert_of[lo + q * CT_WORDS + wi]], (unsigned long long)p);
+            }
+          }
+          ctr[wi] = 0;
+        }
+      } else if (win) {
+        for (uint32_t s = warp; s < nseg; s += NW) {
+          const uint32_t ps = s_ps[s], pe = s_cur[s];
+          for (uint32_t i = ps + lane; i < pe; i += 32) {
+            const uint32_t w = a.mR[i];
+            if (MODE == MODE_SINGLE && w == r) continue;
+            const uint32_t c = Ctr<CW>::take(ctr, w - lo);
+            if (c > 1) {
+              const uint64_t p = pairs_of(c);
+              acc += p;
+              if (MODE == MODE_VERTEX) atomicAdd(&a.bS[a.vert_of[w]], (unsigned long long)p);
+            }
+          }
+        }
+      }
+      acc = warp_sum_u64(acc);
+      if (lane == 0 && acc) atomicAdd(&sh_acc, (unsigned long long)acc);
+      __syncthreads();
+      const uint32_t nm = sh_min;
+      __syncthreads();
+      if (nm == INF_RANK) break;
+      lo = nm;
+      hi = (uint32_t)umin64((uint64_t)a.nS, (uint64_t)lo + Z);
+    }
+    if (threadIdx.x == 0) {
+      localB += sh_acc;
+      if (MODE == MODE_VERTEX && sh_acc) atomicAdd(&a.bS[a.vert_of[r]], sh_acc);
+      if (MODE == MODE_SINGLE) a.bitem[item] = sh_acc;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && localB) atomicAdd(a.B, (unsigned long long)localB);
+}
+
+// ---------------------------------------------------------------------------
+// big class: 32-bit window, segment cursors in global memory (any degree,
+// any number of segments)
+// ---------------------------------------------------------------------------
 template <int MODE>
-__global__ void __launch_bounds__(CT_THREADS, 1) k_cta_class(WArgs a) {
-  extern __shared__ uint32_t ctr[];  // CT_Z counters
-  __shared__ uint32_t s_idx, s_nseg, s_next_min, s_carry;
+__global__ void __launch_bounds__(CT_THREADS, 1) k_cta_big(WArgs a) {
+  extern __shared__ uint32_t ctr[];  // BIG_Z counters
+  __shared__ uint32_t s_idx, s_next_min, s_carry;
   __shared__ unsigned long long s_acc;
+  __shared__ uint32_t wtot[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int NW = CT_THREADS / 32;
   uint32_t *seg = a.seg + (size_t)blockIdx.x * a.seg_cap * 5;
   uint32_t *seg_row = a.seg_row + (size_t)blockIdx.x * a.seg_cap;
-  for (uint32_t i = threadIdx.x; i < CT_Z; i += CT_THREADS) ctr[i] = 0;
+  for (uint32_t i = threadIdx.x; i < BIG_Z; i += CT_THREADS) ctr[i] = 0;
   uint64_t localB = 0;
   __syncthreads();
   while (true) {
     if (threadIdx.x == 0) {
       s_idx = atomicAdd(a.queue, 1u);
-      s_nseg = 0;
       s_carry = 0;
       s_acc = 0;
-      s_next_min = 0xFFFFFFFFu;
+      s_next_min = INF_RANK;
     }
     __syncthreads();
     const uint32_t idx = s_idx;
@@ -249,7 +475,6 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_class(WArgs a) {
     const uint32_t item = a.list[idx];
     const uint32_t r = (MODE == MODE_SINGLE) ? a.item_rank[item] : item;
     const uint64_t rb = a.offR[r], re = a.offR[r + 1];
-    // ---- segments: each start-row entry's suffix cut into pieces of CT_SEG
     for (uint64_t base = rb; base < re; base += CT_THREADS) {
       uint64_t j = base + threadIdx.x;
       uint32_t b = 0, e = 0, ns = 0;
@@ -257,11 +482,9 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_class(WArgs a) {
         const uint32_t x = a.sX[j];
         b = (MODE == MODE_SINGLE) ? (uint32_t)a.offM[x] : a.sB[j];
         e = (uint32_t)a.offM[x + 1];
-        ns = (e - b + CT_SEG - 1) / CT_SEG;
+        ns = (e - b + BIG_SEG - 1) / BIG_SEG;
       }
-      // block exclusive scan of ns
       uint32_t incl = warp_incl_scan_u32(ns);
-      __shared__ uint32_t wtot[NW];
       if (lane == 31) wtot[warp] = incl;
       __syncthreads();
       if (threadIdx.x == 0) {
@@ -276,55 +499,39 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_class(WArgs a) {
         ns = (first < a.seg_cap) ? a.seg_cap - first : 0;
       }
       for (uint32_t k = 0; k < ns; k++) {
-        uint32_t sb = b + k * CT_SEG;
-        uint32_t se = min(e, sb + CT_SEG);
+        uint32_t sb = b + k * BIG_SEG;
+        uint32_t se = min(e, sb + BIG_SEG);
         uint32_t *sg = seg + (size_t)(first + k) * 5;
-        sg[0] = sb; sg[1] = se; sg[2] = sb; sg[3] = sb; sg[4] = 0;  // next = 0: unknown, load it
+        sg[0] = sb; sg[1] = se; sg[2] = sb; sg[3] = sb; sg[4] = 0;
         seg_row[first + k] = (uint32_t)j;
       }
       __syncthreads();
     }
     const uint32_t nseg = min(s_carry, a.seg_cap);
-    // ---- walk the windows
-    uint32_t lo, hi;
-    tile_bounds(a.nS, (MODE == MODE_SINGLE) ? 0u : r + 1, lo, hi);
+    uint32_t lo = (MODE == MODE_SINGLE) ? 0u : r + 1;
+    uint32_t hi = (uint32_t)umin64((uint64_t)a.nS, (uint64_t)lo + BIG_Z);
     while (true) {
-      // count
       for (uint32_t sidx = warp; sidx < nseg; sidx += NW) {
         uint32_t *sg = seg + (size_t)sidx * 5;
         uint32_t pos = sg[2], end = sg[1], nxt = sg[4];
         uint32_t pstart = pos;
         if (pos < end && nxt < hi) {
-          while (pos < end) {
-            uint32_t i = pos + lane;
-            uint32_t w = (i < end) ? a.mR[i] : 0xFFFFFFFFu;
-            bool in = w < hi;
-            uint32_t bal = __ballot_sync(0xffffffffu, in);
-            if (in && (MODE != MODE_SINGLE || w != r)) atomicAdd(&ctr[w - lo], 1u);
-            uint32_t n = __popc(bal);
-            pos += n;
-            if (n < 32) {
-              nxt = __shfl_sync(0xffffffffu, w, n);  // first rank at or above hi (or 0xFFFFFFFF)
-              break;
-            }
-          }
-          if (pos >= end) nxt = 0xFFFFFFFFu;
+          count_segment<MODE, 32>(a.mR, pos, end, lo, hi, r, ctr, nxt);
           if (lane == 0) { sg[2] = pos; sg[3] = pstart; sg[4] = nxt; }
         } else {
-          if (lane == 0) sg[3] = pos;  // nothing this window
-          if (pos >= end) nxt = 0xFFFFFFFFu;
+          if (lane == 0) sg[3] = pos;
+          if (pos >= end) nxt = INF_RANK;
         }
-        if (lane == 0 && nxt != 0xFFFFFFFFu) atomicMin(&s_next_min, nxt);
+        if (lane == 0 && nxt != INF_RANK) atomicMin(&s_next_min, nxt);
       }
       __syncthreads();
-      // VERTEX / EDGE: every wedge of this window reads its final count
-      if (MODE != MODE_TOTAL) {
+      if (MODE == MODE_VERTEX || MODE == MODE_EDGE) {
         for (uint32_t sidx = warp; sidx < nseg; sidx += NW) {
           uint32_t *sg = seg + (size_t)sidx * 5;
           uint32_t ps = sg[3], pe = sg[2];
           if (ps >= pe) continue;
           uint32_t j = seg_row[sidx];
-          long long rowsum = 0;
+          uint64_t rowsum = 0;
           for (uint32_t i = ps + lane; i < pe; i += 32) {
             uint32_t c = ctr[a.mR[i] - lo];
             if (c > 1) {
@@ -332,7 +539,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_class(WArgs a) {
               if (MODE == MODE_EDGE) atomicAdd(&a.be[a.mEid[i]], (unsigned long long)(c - 1));
             }
           }
-          rowsum = warp_sum_i64(rowsum);
+          rowsum = warp_sum_u64(rowsum);
           if (lane == 0 && rowsum) {
             if (MODE == MODE_EDGE) atomicAdd(&a.be[a.sEid[j]], (unsigned long long)rowsum);
             else atomicAdd(&a.bM[a.sX[j]], (unsigned long long)rowsum);
@@ -340,13 +547,13 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_class(WArgs a) {
         }
         __syncthreads();
       }
-      // exchange: collect C(c, 2) once per distinct w and clear the window
       uint64_t acc = 0;
       for (uint32_t sidx = warp; sidx < nseg; sidx += NW) {
         uint32_t *sg = seg + (size_t)sidx * 5;
         uint32_t ps = sg[3], pe = sg[2];
         for (uint32_t i = ps + lane; i < pe; i += 32) {
           uint32_t w = a.mR[i];
+          if (MODE == MODE_SINGLE && w == r) continue;
           uint32_t c = atomicExch(&ctr[w - lo], 0u);
           if (c > 1) {
             uint64_t p = pairs_of(c);
@@ -360,9 +567,10 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_class(WArgs a) {
       __syncthreads();
       const uint32_t nm = s_next_min;
       __syncthreads();
-      if (nm == 0xFFFFFFFFu || nm >= a.nS) break;
-      if (threadIdx.x == 0) s_next_min = 0xFFFFFFFFu;
-      tile_bounds(a.nS, nm, lo, hi);
+      if (nm == INF_RANK) break;
+      if (threadIdx.x == 0) s_next_min = INF_RANK;
+      lo = nm;
+      hi = (uint32_t)umin64((uint64_t)a.nS, (uint64_t)lo + BIG_Z);
       __syncthreads();
     }
     if (threadIdx.x == 0) {
@@ -378,16 +586,25 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_class(WArgs a) {
 // ---------------------------------------------------------------------------
 // classification
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t class_of(uint64_t d, uint64_t w) {
+  if (d < 2 || w == 0) return CLS_SKIP;
+  if (w <= WH_MAX_WORK) return CLS_WARP;
+  if (d + w / SEG + 1 > SMAX) return CLS_BIG;
+  if (d <= 255) return CLS_W8;
+  if (d <= 65535) return CLS_W16;
+  return CLS_W32;
+}
+
 __global__ void k_classify(const uint64_t *offR, const uint64_t *work, uint32_t nS, uint32_t *cls_of,
-                           unsigned int *counts, unsigned long long *maxseg, unsigned long long *cls_sums) {
+                           unsigned int *counts, unsigned long long *maxseg, unsigned long long *sums) {
   for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nS; r += (uint64_t)gridDim.x * blockDim.x) {
-    uint64_t d = offR[r + 1] - offR[r], w = work[r];
-    uint32_t c = (d < 2 || w == 0) ? CLS_SKIP : (w <= WH_MAX_WORK ? CLS_WARP : CLS_CTA);
+    const uint64_t d = offR[r + 1] - offR[r], w = work[r];
+    const uint32_t c = class_of(d, w);
     cls_of[r] = c;
     atomicAdd(&counts[c], 1u);
-    if (w) atomicAdd(&cls_sums[c], (unsigned long long)w);
-    if (d) atomicAdd(&cls_sums[3 + c], (unsigned long long)d);
-    if (c == CLS_CTA) atomicMax(maxseg, (unsigned long long)(d + w / CT_SEG + 1));
+    if (w) atomicAdd(&sums[c], (unsigned long long)w);
+    if (d) atomicAdd(&sums[Plan::NCLS + c], (unsigned long long)d);
+    if (c == CLS_BIG) atomicMax(maxseg, (unsigned long long)(d + w / BIG_SEG + 1));
   }
 }
 __global__ void k_scatter_class(const uint32_t *cls_of, uint32_t nS, const unsigned int *begin, unsigned int *cursor,
@@ -413,12 +630,8 @@ static unsigned grid_for(uint64_t n, unsigned threads, unsigned cap = 152 * 16) 
   return (unsigned)g;
 }
 
-struct ClassMeta {
-  uint32_t seg_cap = 0;
-};
-static ClassMeta g_meta_dummy;
-
 int plan_classify(bfc_graph *g, Plan &p, cudaStream_t s) {
+  constexpr int N = Plan::NCLS;
   const uint32_t nS = p.nS;
   BFC_TRY(dalloc(p.cls, (uint64_t)std::max<uint32_t>(nS, 1) * 4, s));
   DBuf cls_of, cnt, k1, k2, v2;
@@ -426,54 +639,58 @@ int plan_classify(bfc_graph *g, Plan &p, cudaStream_t s) {
   int rc = BFC_OK;
 #define PC_TRY(x) do { rc = (x); if (rc) { cleanup(); return rc; } } while (0)
   PC_TRY(dalloc(cls_of, (uint64_t)std::max<uint32_t>(nS, 1) * 4, s));
-  PC_TRY(dalloc(cnt, 128, s));
-  BFC_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, 128, s));
-  unsigned int *counts = ptr<unsigned int>(cnt);
-  unsigned long long *maxseg = reinterpret_cast<unsigned long long *>(counts + 8);
-  unsigned long long *sums = reinterpret_cast<unsigned long long *>(counts + 16);  // 6 x u64
+  PC_TRY(dalloc(cnt, 256, s));
+  BFC_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, 256, s));
+  unsigned int *counts = ptr<unsigned int>(cnt);                                      // [0, 8)
+  unsigned int *cursor = counts + 8;                                                  // [8, 16)
+  unsigned long long *maxseg = reinterpret_cast<unsigned long long *>(counts + 16);  // 1
+  unsigned long long *sums = reinterpret_cast<unsigned long long *>(counts + 18);    // 2 N
   k_classify<<<grid_for(nS, 256), 256, 0, s>>>(ptr<uint64_t>(p.offR), ptr<uint64_t>(p.work), nS,
                                               ptr<uint32_t>(cls_of), counts, maxseg, sums);
   count_launch();
   unsigned int hc[8];
-  unsigned long long hmax = 0, hs[6];
+  unsigned long long hmax = 0, hs[2 * N];
   BFC_CUDA_TRY(cudaMemcpyAsync(hc, counts, 32, cudaMemcpyDeviceToHost, s));
   BFC_CUDA_TRY(cudaMemcpyAsync(&hmax, maxseg, 8, cudaMemcpyDeviceToHost, s));
-  BFC_CUDA_TRY(cudaMemcpyAsync(hs, sums, 48, cudaMemcpyDeviceToHost, s));
+  BFC_CUDA_TRY(cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, s));
   BFC_CUDA_TRY(cudaStreamSynchronize(s));
-  for (int c = 0; c < 3; c++) { p.cls_work[c] = hs[c]; p.cls_rows[c] = hs[3 + c]; }
   unsigned int hb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int c = 0; c < 3; c++) {
+  for (int c = 0; c < N; c++) {
     p.cls_count[c] = hc[c];
     p.cls_begin[c] = (c == 0) ? 0 : p.cls_begin[c - 1] + p.cls_count[c - 1];
     hb[c] = p.cls_begin[c];
+    p.cls_work[c] = hs[c];
+    p.cls_rows[c] = hs[N + c];
   }
-  p.cls_count[3] = (uint32_t)std::min<unsigned long long>(hmax, 0xFFFFFFFFull);  // segment capacity
+  p.big_seg_cap = (uint32_t)std::min<unsigned long long>(hmax, 0xFFFFFFFFull);
   BFC_CUDA_TRY(cudaMemcpyAsync(counts, hb, 32, cudaMemcpyHostToDevice, s));
-  BFC_CUDA_TRY(cudaMemsetAsync(counts + 8, 0, 32, s));
-  k_scatter_class<<<grid_for(nS, 256), 256, 0, s>>>(ptr<uint32_t>(cls_of), nS, counts, counts + 8,
-                                                   ptr<uint32_t>(p.cls));
+  k_scatter_class<<<grid_for(nS, 256), 256, 0, s>>>(ptr<uint32_t>(cls_of), nS, counts, cursor, ptr<uint32_t>(p.cls));
   count_launch();
-  // heaviest first inside the cta class
-  const uint32_t nc = p.cls_count[CLS_CTA];
-  if (nc > 1) {
-    PC_TRY(dalloc(k1, (uint64_t)nc * 8, s));
-    PC_TRY(dalloc(k2, (uint64_t)nc * 8, s));
-    PC_TRY(dalloc(v2, (uint64_t)nc * 4, s));
-    uint32_t *list = ptr<uint32_t>(p.cls) + p.cls_begin[CLS_CTA];
-    k_work_keys<<<grid_for(nc, 256), 256, 0, s>>>(list, nc, ptr<uint64_t>(p.work), ptr<uint64_t>(k1), list);
-    count_launch();
-    PC_TRY(radix_sort_u64(ptr<uint64_t>(k1), ptr<uint64_t>(k2), list, ptr<uint32_t>(v2), nc, 64, g->scr, s));
-    BFC_CUDA_TRY(cudaMemcpyAsync(list, v2.p, (uint64_t)nc * 4, cudaMemcpyDeviceToDevice, s));
+  // heaviest first inside each window class (better load balance at the tail)
+  uint32_t maxn = 0;
+  for (int c = CLS_W8; c < N; c++) maxn = std::max(maxn, p.cls_count[c]);
+  if (maxn > 1) {
+    PC_TRY(dalloc(k1, (uint64_t)maxn * 8, s));
+    PC_TRY(dalloc(k2, (uint64_t)maxn * 8, s));
+    PC_TRY(dalloc(v2, (uint64_t)maxn * 4, s));
+    for (int c = CLS_W8; c < N; c++) {
+      const uint32_t nc = p.cls_count[c];
+      if (nc < 2) continue;
+      uint32_t *list = ptr<uint32_t>(p.cls) + p.cls_begin[c];
+      k_work_keys<<<grid_for(nc, 256), 256, 0, s>>>(list, nc, ptr<uint64_t>(p.work), ptr<uint64_t>(k1), list);
+      count_launch();
+      PC_TRY(radix_sort_u64(ptr<uint64_t>(k1), ptr<uint64_t>(k2), list, ptr<uint32_t>(v2), nc, 64, g->scr, s));
+      BFC_CUDA_TRY(cudaMemcpyAsync(list, v2.p, (uint64_t)nc * 4, cudaMemcpyDeviceToDevice, s));
+    }
   }
   BFC_CUDA_TRY(cudaStreamSynchronize(s));
   cleanup();
 #undef PC_TRY
-  (void)g_meta_dummy;
   return BFC_OK;
 }
 
 // ---------------------------------------------------------------------------
-// driver
+// launch
 // ---------------------------------------------------------------------------
 static int sm_count() {
   static int n = 0;
@@ -486,51 +703,69 @@ static int sm_count() {
   return n;
 }
 
-static const char *tag_of(int cls, int mode) {
-  static const char *tags[2][3] = {{"warp.total", "warp.vertex", "warp.edge"}, {"cta.total", "cta.vertex", "cta.edge"}};
-  return tags[cls == CLS_CTA ? 1 : 0][mode];
+static const char *tag_of(int kind, int mode) {
+  static const char *tags[3][4] = {{"warp.total", "warp.vertex", "warp.edge", "warp.single"},
+                                   {"win.total", "win.vertex", "win.edge", "win.single"},
+                                   {"big.total", "big.vertex", "big.edge", "big.single"}};
+  return tags[kind][mode];
 }
 
+// class lists: lists[c], counts[c] for c in [0, NCLS)
 template <int MODE>
-static int launch_lists(bfc_graph *g, WArgs a, const uint32_t *warp_list, uint32_t n_warp, const uint32_t *cta_list,
-                        uint32_t n_cta, uint32_t seg_cap, cudaStream_t s) {
+static int launch_lists(bfc_graph *g, WArgs a, const uint32_t *const *lists, const uint32_t *counts, uint32_t big_cap,
+                        cudaStream_t s) {
   const int sms = sm_count();
-  unsigned int *queues = ptr<unsigned int>(g->acc) + 16;  // two counters
-  BFC_CUDA_TRY(cudaMemsetAsync(queues, 0, 8, s));
-  const int tmode = MODE == MODE_SINGLE ? 0 : MODE;
-  if (n_warp) {
+  unsigned int *queues = ptr<unsigned int>(g->acc) + 16;  // one counter per class
+  BFC_CUDA_TRY(cudaMemsetAsync(queues, 0, 4 * Plan::NCLS, s));
+  if (counts[CLS_WARP]) {
     WArgs w = a;
-    w.list = warp_list;
-    w.list_n = n_warp;
-    w.queue = queues;
+    w.list = lists[CLS_WARP];
+    w.list_n = counts[CLS_WARP];
+    w.queue = queues + CLS_WARP;
     const size_t smem = (size_t)WH_WARPS * 2 * WH_SLOTS * 4;
     BFC_CUDA_TRY(cudaFuncSetAttribute(k_warp_class<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
     BFC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_warp_class<MODE>, WH_WARPS * 32, smem));
     unsigned grid = (unsigned)std::max(1, occ) * sms;
     grid = std::min<unsigned>(grid, (w.list_n + WH_WARPS - 1) / WH_WARPS);
-    profile_begin(tag_of(CLS_WARP, tmode), s);
+    profile_begin(tag_of(0, MODE), s);
     k_warp_class<MODE><<<grid, WH_WARPS * 32, smem, s>>>(w);
     BFC_LAUNCHED();
-    profile_end(tag_of(CLS_WARP, tmode), s);
+    profile_end(tag_of(0, MODE), s);
   }
-  if (n_cta) {
+  const bool any_win = counts[CLS_W8] || counts[CLS_W16] || counts[CLS_W32];
+  if (any_win) profile_begin(tag_of(1, MODE), s);
+  for (int c = CLS_W8; c <= CLS_W32; c++) {
+    if (!counts[c]) continue;
+    WArgs w = a;
+    w.list = lists[c];
+    w.list_n = counts[c];
+    w.queue = queues + c;
+    void (*kern)(WArgs) = (c == CLS_W8) ? k_cta_win<MODE, 8> : (c == CLS_W16) ? k_cta_win<MODE, 16>
+                                                                              : k_cta_win<MODE, 32>;
+    BFC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WIN_SMEM));
+    const unsigned grid = std::min<unsigned>((unsigned)sms, w.list_n);
+    kern<<<grid, CT_THREADS, WIN_SMEM, s>>>(w);
+    BFC_LAUNCHED();
+  }
+  if (any_win) profile_end(tag_of(1, MODE), s);
+  if (counts[CLS_BIG]) {
     WArgs c = a;
-    c.list = cta_list;
-    c.list_n = n_cta;
-    c.queue = queues + 1;
-    const size_t smem = (size_t)CT_Z * 4;
-    BFC_CUDA_TRY(cudaFuncSetAttribute(k_cta_class<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    unsigned grid = std::min<unsigned>((unsigned)sms, c.list_n);
-    c.seg_cap = std::max<uint32_t>(seg_cap, 1);
+    c.list = lists[CLS_BIG];
+    c.list_n = counts[CLS_BIG];
+    c.queue = queues + CLS_BIG;
+    const size_t smem = (size_t)BIG_Z * 4;
+    BFC_CUDA_TRY(cudaFuncSetAttribute(k_cta_big<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const unsigned grid = std::min<unsigned>((unsigned)sms, c.list_n);
+    c.seg_cap = std::max<uint32_t>(big_cap, 1);
     const uint64_t need = (uint64_t)grid * c.seg_cap * 6 * 4;
     BFC_TRY(g->scr.reserve(need, s));
     c.seg = static_cast<uint32_t *>(g->scr.base());
     c.seg_row = c.seg + (uint64_t)grid * c.seg_cap * 5;
-    profile_begin(tag_of(CLS_CTA, tmode), s);
-    k_cta_class<MODE><<<grid, CT_THREADS, smem, s>>>(c);
+    profile_begin(tag_of(2, MODE), s);
+    k_cta_big<MODE><<<grid, CT_THREADS, smem, s>>>(c);
     BFC_LAUNCHED();
-    profile_end(tag_of(CLS_CTA, tmode), s);
+    profile_end(tag_of(2, MODE), s);
   }
   return BFC_OK;
 }
@@ -538,8 +773,9 @@ static int launch_lists(bfc_graph *g, WArgs a, const uint32_t *warp_list, uint32
 template <int MODE>
 static int launch_classes(bfc_graph *g, Plan &p, WArgs a, cudaStream_t s) {
   const uint32_t *cls = ptr<uint32_t>(p.cls);
-  return launch_lists<MODE>(g, a, cls + p.cls_begin[CLS_WARP], p.cls_count[CLS_WARP], cls + p.cls_begin[CLS_CTA],
-                            p.cls_count[CLS_CTA], p.cls_count[3], s);
+  const uint32_t *lists[Plan::NCLS];
+  for (int c = 0; c < Plan::NCLS; c++) lists[c] = cls + p.cls_begin[c];
+  return launch_lists<MODE>(g, a, lists, p.cls_count, p.big_seg_cap, s);
 }
 
 static WArgs args_of(bfc_graph *g, Plan &p) {
@@ -577,59 +813,63 @@ __global__ void k_item_classify(const uint32_t *item_rank, uint32_t n, const uin
     w = warp_sum_u64(w);
     if (lane == 0) {
       const uint64_t d = e - b;
-      uint32_t c = (d < 2 || w == 0) ? CLS_SKIP : (w <= WH_MAX_WORK ? CLS_WARP : CLS_CTA);
+      const uint32_t c = class_of(d, w);
       cls_of[i] = c;
       atomicAdd(&counts[c], 1u);
       out[i] = 0;
-      if (c == CLS_CTA) atomicMax(maxseg, (unsigned long long)(d + w / CT_SEG + 1));
+      if (c == CLS_BIG) atomicMax(maxseg, (unsigned long long)(d + w / BIG_SEG + 1));
     }
   }
 }
-__global__ void k_item_scatter(const uint32_t *cls_of, uint32_t n, unsigned int *cursor, uint32_t *warp_list,
-                               uint32_t *cta_list) {
+__global__ void k_item_scatter(const uint32_t *cls_of, uint32_t n, const unsigned int *begin, unsigned int *cursor,
+                               uint32_t *lists) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t c = cls_of[i];
-    if (c == CLS_WARP) warp_list[atomicAdd(&cursor[0], 1u)] = (uint32_t)i;
-    else if (c == CLS_CTA) cta_list[atomicAdd(&cursor[1], 1u)] = (uint32_t)i;
+    const uint32_t c = cls_of[i];
+    if (c == CLS_SKIP) continue;
+    lists[begin[c] + atomicAdd(&cursor[c], 1u)] = (uint32_t)i;
   }
 }
 
 int vbfc_batch(bfc_graph *g, Plan &p, const uint32_t *item_rank, uint32_t n_items, unsigned long long *out,
                cudaStream_t s) {
+  constexpr int N = Plan::NCLS;
   if (n_items == 0) return BFC_OK;
   DBuf cls_of, lists, cnt;
   auto cleanup = [&]() { dfree(cls_of, s); dfree(lists, s); dfree(cnt, s); };
   int rc = BFC_OK;
 #define VB_TRY(x) do { rc = (x); if (rc) { cleanup(); return rc; } } while (0)
   VB_TRY(dalloc(cls_of, (uint64_t)n_items * 4, s));
-  VB_TRY(dalloc(lists, (uint64_t)n_items * 8, s));
-  VB_TRY(dalloc(cnt, 64, s));
-  BFC_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, 64, s));
-  unsigned int *counts = ptr<unsigned int>(cnt);
-  unsigned long long *maxseg = reinterpret_cast<unsigned long long *>(counts + 4);
+  VB_TRY(dalloc(lists, (uint64_t)n_items * 4, s));
+  VB_TRY(dalloc(cnt, 128, s));
+  BFC_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, 128, s));
+  unsigned int *counts = ptr<unsigned int>(cnt);                                      // [0, 8)
+  unsigned int *begin = counts + 8;                                                   // [8, 16)
+  unsigned int *cursor = counts + 16;                                                 // [16, 24)
+  unsigned long long *maxseg = reinterpret_cast<unsigned long long *>(counts + 24);
   k_item_classify<<<grid_for((uint64_t)n_items * 32, 256), 256, 0, s>>>(item_rank, n_items, ptr<uint64_t>(p.offR),
                                                                         ptr<uint32_t>(p.sX), p.offM,
                                                                         ptr<uint32_t>(cls_of), counts, maxseg, out);
   count_launch();
-  unsigned int hc[4];
+  unsigned int hc[8];
   unsigned long long hmax = 0;
-  BFC_CUDA_TRY(cudaMemcpyAsync(hc, counts, 16, cudaMemcpyDeviceToHost, s));
+  BFC_CUDA_TRY(cudaMemcpyAsync(hc, counts, 32, cudaMemcpyDeviceToHost, s));
   BFC_CUDA_TRY(cudaMemcpyAsync(&hmax, maxseg, 8, cudaMemcpyDeviceToHost, s));
   BFC_CUDA_TRY(cudaStreamSynchronize(s));
-  uint32_t *warp_list = ptr<uint32_t>(lists);
-  uint32_t *cta_list = warp_list + n_items;
-  BFC_CUDA_TRY(cudaMemsetAsync(counts + 8, 0, 8, s));
-  k_item_scatter<<<grid_for(n_items, 256), 256, 0, s>>>(ptr<uint32_t>(cls_of), n_items, counts + 8, warp_list,
-                                                       cta_list);
+  unsigned int hb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  uint32_t run = 0;
+  for (int c = 1; c < N; c++) { hb[c] = run; run += hc[c]; }
+  BFC_CUDA_TRY(cudaMemcpyAsync(begin, hb, 32, cudaMemcpyHostToDevice, s));
+  k_item_scatter<<<grid_for(n_items, 256), 256, 0, s>>>(ptr<uint32_t>(cls_of), n_items, begin, cursor,
+                                                       ptr<uint32_t>(lists));
   count_launch();
   WArgs a = args_of(g, p);
   a.item_rank = item_rank;
   a.bitem = out;
-  unsigned long long dummyB_off = 0;
-  (void)dummyB_off;
   a.B = ptr<unsigned long long>(g->acc) + 1;  // not read back
-  VB_TRY(launch_lists<MODE_SINGLE>(g, a, warp_list, hc[CLS_WARP], cta_list, hc[CLS_CTA],
-                                   (uint32_t)std::min<unsigned long long>(hmax, 0xFFFFFFFFull), s));
+  const uint32_t *L[N];
+  uint32_t C[N];
+  for (int c = 0; c < N; c++) { L[c] = ptr<uint32_t>(lists) + hb[c]; C[c] = (c == 0) ? 0 : hc[c]; }
+  VB_TRY(launch_lists<MODE_SINGLE>(g, a, L, C, (uint32_t)std::min<unsigned long long>(hmax, 0xFFFFFFFFull), s));
   cleanup();
 #undef VB_TRY
   return BFC_OK;
@@ -646,8 +886,8 @@ int wedge_count(bfc_graph *g, Plan &p, Mode mode, unsigned long long *d_B, uint6
     case MODE_TOTAL: return launch_classes<MODE_TOTAL>(g, p, a, s);
     case MODE_VERTEX: return launch_classes<MODE_VERTEX>(g, p, a, s);
     case MODE_EDGE: return launch_classes<MODE_EDGE>(g, p, a, s);
+    default: return BFC_EINVAL;
   }
-  return BFC_EINVAL;
 }
 
 }  // namespace bfc
