@@ -5,8 +5,9 @@ Chung-Lu bipartite graph |U| = 1M, |V| = 5M, 50M distinct edges, exponents
 
 One step = the whole counting path on the device-resident edge list: graph
 build (sort, validate, both adjacency structures), degree statistics and side
-choice (Algorithm 1), rank layout and classes, ExactBFC (B), vBFC for every
-vertex and eBFC for every edge.  Metric: wedges/s, where a step's wedges are
+choice (Algorithm 1), rank layout and classes, ExactBFC (B, the ordered
+one-sided sweep) and one whole-row sweep that gives vBFC for every vertex and
+eBFC for every edge (bfc_local_counts).  Metric: wedges/s, where a step's wedges are
 W = sum over the midpoint side of C(d, 2) (Lemma 2: the work of Algorithm 1).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl own|reference]
@@ -194,14 +195,17 @@ def run_own(args, rank, world, local_rank):
     Bh = ctypes.c_uint64()
     side_h = ctypes.c_int()
 
+    B2h = ctypes.c_uint64()
+
     def step():
         h = bfc.bfc_graph_from_edges(du, dv, nU, nV, 0, sptr)
         try:
             bfc._check(L.bfc_exact(h, 0, ctypes.byref(Bh), ctypes.byref(side_h), sptr), "bfc_exact")
-            bfc._check(L.bfc_per_vertex(h, 0, bU.data_ptr(), bV.data_ptr(), None, sptr), "bfc_per_vertex")
-            bfc._check(L.bfc_per_edge(h, 0, be.data_ptr(), None, sptr), "bfc_per_edge")
+            bfc._check(L.bfc_local_counts(h, 0, bU.data_ptr(), bV.data_ptr(), be.data_ptr(), ctypes.byref(B2h), sptr),
+                       "bfc_local_counts")
         finally:
             bfc.bfc_graph_free(h)
+        assert B2h.value == Bh.value
         return int(Bh.value), int(side_h.value)
 
     # statistics of the workload (not timed)
@@ -255,8 +259,8 @@ def run_own(args, rank, world, local_rank):
         h = hh.value
         try:
             bfc._check(L.bfc_exact(h, 0, ctypes.byref(Bh), ctypes.byref(side_h), sptr), "bfc_exact")
-            bfc._check(L.bfc_per_vertex(h, 0, bU.data_ptr(), bV.data_ptr(), None, sptr), "bfc_per_vertex")
-            bfc._check(L.bfc_per_edge(h, 0, be.data_ptr(), None, sptr), "bfc_per_edge")
+            bfc._check(L.bfc_local_counts(h, 0, bU.data_ptr(), bV.data_ptr(), be.data_ptr(), ctypes.byref(B2h), sptr),
+                       "bfc_local_counts")
             obU.copy_(bU, non_blocking=True)
             obV.copy_(bV, non_blocking=True)
             obe.copy_(be, non_blocking=True)
@@ -286,7 +290,10 @@ def run_own(args, rank, world, local_rank):
     mode = dom.split(".")[1]
     wedges = sum(ps["work"][c] for c in bfc.TAG_CLASSES[cls])
     rows = sum(ps["rows"][c] for c in bfc.TAG_CLASSES[cls])
-    per_wedge = 8 if mode == "edge" else 4
+    if mode in ("local", "single"):
+        # whole rows: every wedge is walked from both ends
+        wedges = 2 * wedges
+    per_wedge = 8 if mode in ("edge", "local") else 4
     alg_bytes = per_wedge * wedges + 16 * rows
     avg_ms = tot_ms / max(n_launch, 1)
     achieved = alg_bytes / (avg_ms / 1e3) / 1e9

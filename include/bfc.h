@@ -57,6 +57,13 @@ extern "C" {
 #define BFC_SIDE_AUTO     0x0u
 #define BFC_SIDE_U        0x10u
 #define BFC_SIDE_V        0x20u
+/* bfc_per_vertex / bfc_per_edge / bfc_local_counts: count with whole-row
+ * sweeps (Algorithm 2 for every start vertex: every pair seen from both ends,
+ * every output written by its owner) instead of the default one-sided ordered
+ * sweep of Algorithm 1 (each pair once, the far endpoint's outputs updated
+ * with scattered atomics).  Same results; the cost differs with the degree
+ * skew. */
+#define BFC_WHOLE_ROWS    0x100u
 
 typedef struct bfc_graph bfc_graph;
 typedef struct bfc_proposal bfc_proposal;
@@ -115,6 +122,21 @@ int bfc_per_vertex(bfc_graph *g, uint32_t flags, uint64_t *bU, uint64_t *bV, uin
  * out_B (host, may be NULL): B. */
 int bfc_per_edge(bfc_graph *g, uint32_t flags, uint64_t *be, uint64_t *out_B, void *stream);
 
+/* vBFC and eBFC together in one sweep (Algorithm 2's counts for every vertex
+ * and the per-edge counts of Section 2).  Default: the ordered sweep of
+ * Algorithm 1, where each pair {v, w} of start vertices with c = |Gamma_v ^
+ * Gamma_w| adds C(c, 2) to b_v and b_w, and each wedge v - x - w adds c - 1
+ * to b_x, b_(v,x) and b_(w,x).  BFC_WHOLE_ROWS: Algorithm 2 for every start
+ * vertex v gives b_v and the row sums b_(v,x) = sum over w in Gamma_x \ {v}
+ * of (c(v, w) - 1), and the midpoint side gets b_x = 1/2 sum of b_e over x's
+ * edges.
+ *   bU, bV : device, nU / nV entries (either may be NULL)
+ *   be     : device, m entries, canonical order (may be NULL)
+ *   out_B  : host, B (may be NULL).
+ * Errors as bfc_exact. */
+int bfc_local_counts(bfc_graph *g, uint32_t flags, uint64_t *bU, uint64_t *bV, uint64_t *be, uint64_t *out_B,
+                     void *stream);
+
 /* ---- sparsification (Section 6) --------------------------------------- */
 
 /* ESpar (Algorithm 8), `trials` independent trials.  Trial t keeps canonical
@@ -165,10 +187,11 @@ int bfc_proposal_free(bfc_proposal *p);
 
 /* Work split of the start side `side` (0 = U, 1 = V) after its layout is
  * built (any counting call builds it; this call builds it if needed).
- * out (host, 20 entries): out[0] = nS; then for the six kernel classes
- * skip / warp / win8 / win16 / win32 / big: vertex counts out[1..6], wedges
- * walked out[7..12], start-row entries out[13..18]; out[19] = total wedges W
- * of the midpoint side (Lemma 2). */
+ * out (host, 41 entries): out[0] = nS; then for the 13 kernel classes
+ * skip, warp, small windows with 2/4/8/16/32-bit counters, large windows
+ * with 2/4/8/16/32-bit counters, big: vertex counts out[1..13], wedges walked
+ * out[14..26], start-row entries out[27..39]; out[40] = total wedges W of
+ * the midpoint side (Lemma 2). */
 int bfc_plan_stats(bfc_graph *g, int side, uint64_t *out, void *stream);
 
 /* Device timing of the library's counting kernels: when enabled, every
@@ -176,7 +199,7 @@ int bfc_plan_stats(bfc_graph *g, int side, uint64_t *out, void *stream);
  * bfc_profile_read synchronises on the recorded events and returns, for the
  * kernel tag (e.g. "win.total", "warp.vertex", "big.edge"), the number of
  * launches and their summed device time in milliseconds.  Tags:
- * {warp,win,big}.{total,vertex,edge,single}. */
+ * {warp,win,big}.{total,vertex,edge,single,local}. */
 int bfc_profile_enable(int on);
 int bfc_profile_reset(void);
 int bfc_profile_read(const char *tag, uint64_t *launches, double *total_ms);

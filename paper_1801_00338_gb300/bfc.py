@@ -27,6 +27,7 @@ BFC_DEDUP = 0x2
 BFC_SIDE_AUTO = 0x0
 BFC_SIDE_U = 0x10
 BFC_SIDE_V = 0x20
+BFC_WHOLE_ROWS = 0x100
 
 _lib = None
 
@@ -54,6 +55,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "bfc_exact": [P, u32, P, P, P],
         "bfc_per_vertex": [P, u32, P, P, P, P],
         "bfc_per_edge": [P, u32, P, P, P],
+        "bfc_local_counts": [P, u32, P, P, P, P, P],
         "bfc_espar": [P, dbl, u32, u64, P, P, P],
         "bfc_clrspar": [P, u32, u32, u64, P, P, P],
         "bfc_vsamp": [P, u64, P, u32, u64, P, P, P, P],
@@ -112,12 +114,12 @@ def bfc_launch_count() -> int:
     return int(load().bfc_launch_count())
 
 
-CLASSES = ("skip", "warp", "win8", "win16", "win32", "big")
+CLASSES = ("skip", "warp", "s2", "s4", "s8", "s16", "s32", "l2", "l4", "l8", "l16", "l32", "big")
 
 
 def bfc_plan_stats(h: int, side: int, stream=None) -> dict:
     """Per-class vertex counts, wedges and start-row entries of a start side's layout."""
-    out = np.zeros(20, np.uint64)
+    out = np.zeros(41, np.uint64)
     _check(load().bfc_plan_stats(h, side, out.ctypes.data, _stream_ptr(stream)), "bfc_plan_stats")
     o = [int(x) for x in out]
     n = len(CLASSES)
@@ -140,9 +142,10 @@ def bfc_profile_read(tag: str) -> tuple[int, float]:
     return int(n.value), float(ms.value)
 
 
-PROFILE_TAGS = [f"{c}.{m}" for c in ("warp", "win", "big") for m in ("total", "vertex", "edge", "single")]
+PROFILE_TAGS = [f"{c}.{m}" for c in ("warp", "win", "big") for m in ("total", "vertex", "edge", "single", "local")]
 # kernel tag -> the classes it runs
-TAG_CLASSES = {"warp": ("warp",), "win": ("win8", "win16", "win32"), "big": ("big",)}
+TAG_CLASSES = {"warp": ("warp",), "win": ("s2", "s4", "s8", "s16", "s32", "l2", "l4", "l8", "l16", "l32"),
+               "big": ("big",)}
 
 
 # ----------------------------------------------------------------------------
@@ -217,6 +220,17 @@ def bfc_per_edge(h: int, m: int, flags: int = 0, stream=None):
     return be[:m], int(B.value)
 
 
+def bfc_local_counts(h: int, nU: int, nV: int, m: int, flags: int = 0, stream=None):
+    import torch
+    bU = torch.empty(nU, dtype=torch.int64, device="cuda")
+    bV = torch.empty(nV, dtype=torch.int64, device="cuda")
+    be = torch.empty(max(m, 1), dtype=torch.int64, device="cuda")
+    B = ctypes.c_uint64()
+    _check(load().bfc_local_counts(h, flags, _dptr(bU), _dptr(bV), _dptr(be), ctypes.byref(B), _stream_ptr(stream)),
+           "bfc_local_counts")
+    return bU, bV, be[:m], int(B.value)
+
+
 def bfc_espar(h: int, p: float, trials: int, seed: int, stream=None):
     est = np.zeros(trials, np.float64)
     beta = np.zeros(trials, np.uint64)
@@ -286,11 +300,15 @@ class Graph:
     def exact(self, side=None, stream=None):
         return bfc_exact(self.h, _SIDE[side], stream)
 
-    def per_vertex(self, side=None, stream=None):
-        return bfc_per_vertex(self.h, self.nU, self.nV, _SIDE[side], stream)
+    def per_vertex(self, side=None, whole_rows=False, stream=None):
+        return bfc_per_vertex(self.h, self.nU, self.nV, _SIDE[side] | (BFC_WHOLE_ROWS if whole_rows else 0), stream)
 
-    def per_edge(self, side=None, stream=None):
-        return bfc_per_edge(self.h, self.m, _SIDE[side], stream)
+    def per_edge(self, side=None, whole_rows=False, stream=None):
+        return bfc_per_edge(self.h, self.m, _SIDE[side] | (BFC_WHOLE_ROWS if whole_rows else 0), stream)
+
+    def local_counts(self, side=None, whole_rows=False, stream=None):
+        return bfc_local_counts(self.h, self.nU, self.nV, self.m, _SIDE[side] | (BFC_WHOLE_ROWS if whole_rows else 0),
+                                stream)
 
     def plan_stats(self, side: int, stream=None):
         return bfc_plan_stats(self.h, side, stream)

@@ -122,7 +122,7 @@ struct Plan {
   DBuf work;             // u64[nS]  ordered wedges walked from each start rank
   // vertex classes (ranks), see wedge.cu
   DBuf cls;              // u32[nS]  ranks grouped by class
-  static constexpr int NCLS = 6;      // skip, warp, win8, win16, win32, big (wedge.cu)
+  static constexpr int NCLS = 13;     // skip, warp, 5 small windows, 5 large windows, big (wedge.cu)
   uint32_t cls_count[NCLS] = {};
   uint32_t cls_begin[NCLS] = {};
   uint64_t cls_work[NCLS] = {};       // wedges walked per class
@@ -156,7 +156,7 @@ int choose_side(const bfc_graph *g, uint32_t flags);
 int read_device_error(bfc_graph *g, cudaStream_t s);  // maps DERR_* bits to a status and clears
 
 // wedge.cu
-enum Mode { MODE_TOTAL = 0, MODE_VERTEX = 1, MODE_EDGE = 2, MODE_SINGLE = 3 };
+enum Mode { MODE_TOTAL = 0, MODE_VERTEX = 1, MODE_EDGE = 2, MODE_SINGLE = 3, MODE_LOCAL = 4 };
 // Counts with the start side of plan p.  out_B receives B (device u64).
 // bS / bM: per-vertex outputs of the start / midpoint side (device, original
 // ids) or null; be: per-edge output (canonical ids) or null.
@@ -168,6 +168,11 @@ void plan_free(Plan &p, cudaStream_t s);
 // at rank item_rank[i] (every other start vertex w != v, full midpoint rows).
 int vbfc_batch(bfc_graph *g, Plan &p, const uint32_t *item_rank, uint32_t n_items, unsigned long long *out,
                cudaStream_t s);
+// Local counts in one pass over whole midpoint rows (Algorithm 2 for every
+// start vertex): bS[v] = b_v, be[e] = b_e (each optional), bM[x] = b_x of the
+// midpoint side from be (needs be), and d_2B += 2B (Lemma 1, Eq. (1)).
+int wedge_local(bfc_graph *g, Plan &p, unsigned long long *d_2B, uint64_t *bS, uint64_t *bM, uint64_t *be,
+                cudaStream_t s);
 // Filter plan `parent` to the canonical edges with keep[e] != 0 into `out`
 // (same start side and rank order; rows stay sorted).
 int plan_filter(bfc_graph *g, const Plan &parent, const uint32_t *keep, Plan &out, cudaStream_t s);

@@ -1,4 +1,5 @@
 // C ABI entry points (declared in include/bfc.h).
+#include <algorithm>
 #include <new>
 
 #include "bfc_internal.cuh"
@@ -33,6 +34,7 @@ int finish_count(bfc_graph *g, uint64_t *out_B, cudaStream_t s) {
 int prepare(bfc_graph *g, uint32_t flags, cudaStream_t s, int *side) {
   if (!g) return BFC_EINVAL;
   if ((flags & BFC_SIDE_U) && (flags & BFC_SIDE_V)) return BFC_EINVAL;
+  if (flags & ~(BFC_SIDE_U | BFC_SIDE_V | BFC_WHOLE_ROWS)) return BFC_EINVAL;
   *side = choose_side(g, flags);
   BFC_TRY(plan_build(g, *side, s));
   g->last_stream = s;
@@ -117,32 +119,81 @@ int bfc_exact(bfc_graph *g, uint32_t flags, uint64_t *out_B, int *out_side, void
   return BFC_OK;
 }
 
-int bfc_per_vertex(bfc_graph *g, uint32_t flags, uint64_t *bU, uint64_t *bV, uint64_t *out_B, void *stream) {
-  cudaStream_t s = as_stream(stream);
+// The whole-row sweep (BFC_WHOLE_ROWS).
+static int whole_rows(bfc_graph *g, uint32_t flags, uint64_t *bU, uint64_t *bV, uint64_t *be, uint64_t *out_B,
+                      cudaStream_t s) {
   int side = 0;
   BFC_TRY(prepare(g, flags, s, &side));
+  uint64_t *bS = side ? bV : bU;
+  uint64_t *bM = side ? bU : bV;
+  DBuf tmp;
+  uint64_t *pe = be;
+  if (bM && !be) {
+    BFC_TRY(dalloc(tmp, std::max<uint64_t>(g->m, 1) * 8, s));
+    pe = ptr<uint64_t>(tmp);
+  }
+  int rc = wedge_local(g, g->plan[side], acc_B(g), bS, bM, pe, s);
+  uint64_t twoB = 0;
+  if (rc == BFC_OK) rc = finish_count(g, &twoB, s);
+  dfree(tmp, s);
+  if (rc != BFC_OK) return rc;
+  if (twoB & 1) return BFC_EINTERNAL;  // Eq. (1): the start side counts every butterfly twice
+  if (out_B) *out_B = twoB / 2;
+  return BFC_OK;
+}
+
+// The ordered one-sided sweep: per-vertex outputs (both sides) and/or per-edge outputs.
+static int ordered_local(bfc_graph *g, uint32_t flags, uint64_t *bU, uint64_t *bV, uint64_t *be, uint64_t *out_B,
+                         cudaStream_t s) {
+  int side = 0;
+  BFC_TRY(prepare(g, flags, s, &side));
+  if (be && g->m > 0) BFC_CUDA_TRY(cudaMemsetAsync(be, 0, g->m * 8, s));
+  if (!bU && !bV) {
+    BFC_TRY(wedge_count(g, g->plan[side], MODE_EDGE, acc_B(g), nullptr, nullptr, be, s));
+    return finish_count(g, out_B, s);
+  }
   DBuf tmpU, tmpV;
-  if (!bU) BFC_TRY(dalloc(tmpU, (uint64_t)g->nU * 8, s));
-  if (!bV) BFC_TRY(dalloc(tmpV, (uint64_t)g->nV * 8, s));
+  int rc = BFC_OK;
+  if (!bU) rc = dalloc(tmpU, (uint64_t)g->nU * 8, s);
+  if (!rc && !bV) rc = dalloc(tmpV, (uint64_t)g->nV * 8, s);
   uint64_t *pU = bU ? bU : ptr<uint64_t>(tmpU);
   uint64_t *pV = bV ? bV : ptr<uint64_t>(tmpV);
-  BFC_CUDA_TRY(cudaMemsetAsync(pU, 0, (uint64_t)g->nU * 8, s));
-  BFC_CUDA_TRY(cudaMemsetAsync(pV, 0, (uint64_t)g->nV * 8, s));
-  int rc = wedge_count(g, g->plan[side], MODE_VERTEX, acc_B(g), side ? pV : pU, side ? pU : pV, nullptr, s);
-  if (rc == BFC_OK) rc = finish_count(g, out_B, s);
+  if (!rc && cudaMemsetAsync(pU, 0, (uint64_t)g->nU * 8, s) != cudaSuccess) rc = BFC_ECUDA;
+  if (!rc && cudaMemsetAsync(pV, 0, (uint64_t)g->nV * 8, s) != cudaSuccess) rc = BFC_ECUDA;
+  if (!rc) rc = wedge_count(g, g->plan[side], MODE_VERTEX, acc_B(g), side ? pV : pU, side ? pU : pV, be, s);
+  if (!rc) rc = finish_count(g, out_B, s);
   dfree(tmpU, s);
   dfree(tmpV, s);
   return rc;
 }
 
-int bfc_per_edge(bfc_graph *g, uint32_t flags, uint64_t *be, uint64_t *out_B, void *stream) {
-  if (!be && g && g->m > 0) return BFC_EINVAL;
+int bfc_local_counts(bfc_graph *g, uint32_t flags, uint64_t *bU, uint64_t *bV, uint64_t *be, uint64_t *out_B,
+                     void *stream) {
+  if (!g) return BFC_EINVAL;
   cudaStream_t s = as_stream(stream);
-  int side = 0;
-  BFC_TRY(prepare(g, flags, s, &side));
-  if (g->m > 0) BFC_CUDA_TRY(cudaMemsetAsync(be, 0, g->m * 8, s));
-  BFC_TRY(wedge_count(g, g->plan[side], MODE_EDGE, acc_B(g), nullptr, nullptr, be, s));
-  return finish_count(g, out_B, s);
+  if (flags & BFC_WHOLE_ROWS) return whole_rows(g, flags, bU, bV, be, out_B, s);
+  return ordered_local(g, flags, bU, bV, be, out_B, s);
+}
+
+int bfc_per_vertex(bfc_graph *g, uint32_t flags, uint64_t *bU, uint64_t *bV, uint64_t *out_B, void *stream) {
+  if (!g) return BFC_EINVAL;
+  cudaStream_t s = as_stream(stream);
+  if (!(flags & BFC_WHOLE_ROWS)) return ordered_local(g, flags, bU, bV, nullptr, out_B, s);
+  DBuf tU, tV;
+  uint64_t *pU = bU, *pV = bV;
+  if (!pU) { BFC_TRY(dalloc(tU, (uint64_t)g->nU * 8, s)); pU = ptr<uint64_t>(tU); }
+  if (!pV) { BFC_TRY(dalloc(tV, (uint64_t)g->nV * 8, s)); pV = ptr<uint64_t>(tV); }
+  int rc = whole_rows(g, flags, pU, pV, nullptr, out_B, s);
+  dfree(tU, s);
+  dfree(tV, s);
+  return rc;
+}
+
+int bfc_per_edge(bfc_graph *g, uint32_t flags, uint64_t *be, uint64_t *out_B, void *stream) {
+  if (!g || (!be && g->m > 0)) return BFC_EINVAL;
+  cudaStream_t s = as_stream(stream);
+  if (flags & BFC_WHOLE_ROWS) return whole_rows(g, flags, nullptr, nullptr, be, out_B, s);
+  return ordered_local(g, flags, nullptr, nullptr, be, out_B, s);
 }
 
 int bfc_plan_stats(bfc_graph *g, int side, uint64_t *out, void *stream) {

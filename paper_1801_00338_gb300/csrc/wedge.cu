@@ -11,18 +11,23 @@
 // vBFC costs O(|Gamma^2_v|)) and by their degree (which bounds every c(v, w)):
 //   skip   degree < 2 or nothing after it: every c <= 1, contributes 0
 //   warp   <= 512 wedges: one warp per vertex, open addressing in shared memory
-//   win8   degree <= 255: one CTA per vertex, dense 8-bit counters in shared
-//          memory over a window of 196,608 consecutive ranks
-//   win16  degree <= 65,535: the same with 16-bit counters (98,304 ranks)
-//   win32  the same with 32-bit counters (49,152 ranks)
+//   win2   degree <= 3: one CTA per vertex, dense 2-bit counters in shared
+//          memory over a window of 786,432 consecutive ranks
+//   win4   degree <= 15: 4-bit counters (393,216 ranks)
+//   win8   degree <= 255: 8-bit counters (196,608 ranks)
+//   win16  degree <= 65,535: 16-bit counters (98,304 ranks)
+//   win32  32-bit counters (49,152 ranks)
+// Ranks ascend with degree, so the low-rank vertices, which walk the most of
+// the rank space, are exactly the ones with the narrowest counters and the
+// widest windows.
 //   big    more wedge-list segments than shared memory holds: the window kernel
 //          with its segment cursors in global memory
 // A window kernel walks the ranks after r window by window; a window starts at
 // the lowest rank still pending in any of the vertex's (rank-sorted) wedge
 // lists, so empty rank ranges cost nothing.  Each window has a count sweep
-// (shared-memory atomic increments) and an exchange sweep that reads C(c, 2)
-// once per distinct w and clears the counters: by re-walking the window's
-// wedges when they are few, or by scanning the counter words when they are many.
+// (shared-memory atomic increments whose old values sum to sum_w C(c, 2)) and
+// a clear of the counter words; VERTEX mode instead re-walks the window's
+// wedges, taking each distinct target's final count once as it clears it.
 //
 // Modes: TOTAL (B only), VERTEX (b for both sides), EDGE (b_e), SINGLE
 // (Algorithm 2 on a batch of vertices: every w != v, whole midpoint rows).
@@ -41,20 +46,33 @@ namespace bfc {
 
 constexpr uint32_t EMPTY_KEY = 0xFFFFFFFFu;
 constexpr uint32_t INF_RANK = 0xFFFFFFFFu;
-enum Cls : uint32_t { CLS_SKIP = 0, CLS_WARP = 1, CLS_W8 = 2, CLS_W16 = 3, CLS_W32 = 4, CLS_BIG = 5 };
+// class ids: skip, warp, then small windows for counter widths 2/4/8/16/32,
+// large windows for the same widths, then big
+enum Cls : uint32_t { CLS_SKIP = 0, CLS_WARP = 1, CLS_S0 = 2, CLS_L0 = 7, CLS_BIG = 12 };
+static_assert(CLS_BIG + 1 == Plan::NCLS, "class count");
+constexpr int CW_OF[5] = {2, 4, 8, 16, 32};
 
 // warp class
 constexpr int WH_WARPS = 8;
 constexpr int WH_SLOTS = 1024;                    // per warp
 constexpr uint64_t WH_MAX_WORK = WH_SLOTS / 2;    // load factor <= 1/2
-// window classes
+// window kernels come in two sizes: P CTAs of 1024/P threads per SM, each
+// with 49,152/P counter words and room for 1,536/P wedge-list segments.
+// Small (P = 4) keeps four vertices in flight per SM to hide the latency of
+// the dependent loads every window starts with; large (P = 1) takes the
+// vertices whose wedge lists need more segments.
+template <int P>
+struct WinCfg {
+  static constexpr int THREADS = 1024 / P;
+  static constexpr uint32_t WORDS = 48 * 1024 / P;
+  static constexpr uint32_t SMAX = 1536 / P;
+  static constexpr size_t SMEM = (size_t)WORDS * 4 + (size_t)SMAX * 5 * 4;
+};
+constexpr int P_SMALL = 4, P_LARGE = 1;
+constexpr uint32_t SEG = 256;                     // wedge-list segment (elements)
+// big class (segment cursors in global memory)
 constexpr int CT_THREADS = 1024;
 constexpr uint32_t CT_WORDS = 48 * 1024;          // 192 KB of counter words
-constexpr uint32_t SEG = 1024;                    // wedge-list segment (elements)
-constexpr uint32_t SMAX = 1536;                   // segments held in shared memory
-constexpr uint32_t DENSE_MIN = CT_WORDS / 2;      // window wedges above which the exchange scans words
-constexpr size_t WIN_SMEM = (size_t)CT_WORDS * 4 + (size_t)SMAX * 5 * 4;
-// big class (segment cursors in global memory)
 constexpr uint32_t BIG_SEG = 256;
 constexpr uint32_t BIG_Z = CT_WORDS;
 
@@ -81,6 +99,9 @@ struct WArgs {
 };
 
 __device__ __forceinline__ uint64_t umin64(uint64_t x, uint64_t y) { return x < y ? x : y; }
+// modes that walk whole midpoint rows (every w != v) rather than the part after v
+template <int MODE>
+struct Full { static constexpr bool value = (MODE == MODE_SINGLE || MODE == MODE_LOCAL); };
 __device__ __forceinline__ uint64_t pairs_of(uint32_t c) { return (uint64_t)c * (c - (c > 0)) / 2; }
 
 __device__ __forceinline__ uint32_t warp_incl_scan_u32(uint32_t x) {
@@ -179,9 +200,9 @@ __global__ void __launch_bounds__(WH_WARPS * 32) k_warp_class(WArgs a) {
     const uint32_t item = a.list[idx];
     const uint32_t r = (MODE == MODE_SINGLE) ? a.item_rank[item] : item;
     const uint64_t rb = a.offR[r], re = a.offR[r + 1];
-    warp_for_each_wedge<MODE == MODE_SINGLE>(a, rb, re, [&](uint32_t i, uint64_t) {
+    warp_for_each_wedge<Full<MODE>::value>(a, rb, re, [&](uint32_t i, uint64_t) {
       const uint32_t w = a.mR[i];
-      if (MODE != MODE_SINGLE || w != r) wh_insert(keys, cnts, w);
+      if (!Full<MODE>::value || w != r) wh_insert(keys, cnts, w);
     });
     __syncwarp();
     if (MODE == MODE_VERTEX || MODE == MODE_EDGE) {
@@ -189,13 +210,20 @@ __global__ void __launch_bounds__(WH_WARPS * 32) k_warp_class(WArgs a) {
       warp_for_each_wedge<false>(a, rb, re, [&](uint32_t i, uint64_t j) {
         uint32_t c = wh_lookup(keys, cnts, a.mR[i]);
         if (c > 1) {
-          if (MODE == MODE_EDGE) {
+          if (a.be) {
             atomicAdd(&a.be[a.mEid[i]], (unsigned long long)(c - 1));
             atomicAdd(&a.be[a.sEid[j]], (unsigned long long)(c - 1));
-          } else {
-            atomicAdd(&a.bM[a.sX[j]], (unsigned long long)(c - 1));
           }
+          if (MODE == MODE_VERTEX) atomicAdd(&a.bM[a.sX[j]], (unsigned long long)(c - 1));
         }
+      });
+      __syncwarp();
+    }
+    if (MODE == MODE_LOCAL && a.be) {
+      // b_(v,x) = sum over w in Gamma_x, w != v, of (c(v, w) - 1)
+      warp_for_each_wedge<true>(a, rb, re, [&](uint32_t i, uint64_t j) {
+        const uint32_t c = wh_lookup(keys, cnts, a.mR[i]);
+        if (c > 1) atomicAdd(&a.be[a.sEid[j]], (unsigned long long)(c - 1));
       });
       __syncwarp();
     }
@@ -215,6 +243,7 @@ __global__ void __launch_bounds__(WH_WARPS * 32) k_warp_class(WArgs a) {
       localB += acc;
       if (MODE == MODE_VERTEX && acc) atomicAdd(&a.bS[a.vert_of[r]], (unsigned long long)acc);
       if (MODE == MODE_SINGLE) a.bitem[item] = acc;
+      if (MODE == MODE_LOCAL && a.bS) a.bS[a.vert_of[r]] = acc;
     }
     __syncwarp();
   }
@@ -224,24 +253,30 @@ __global__ void __launch_bounds__(WH_WARPS * 32) k_warp_class(WArgs a) {
 // ---------------------------------------------------------------------------
 // window classes: packed dense counters in shared memory
 // ---------------------------------------------------------------------------
-// Counter of window offset idx: word idx mod CT_WORDS, field idx / CT_WORDS,
+// Counter of window offset idx: word idx mod WIN_WORDS, field idx / WIN_WORDS,
 // so consecutive ranks (a sorted wedge list) fall in consecutive words and
 // different banks.  A CW-bit field cannot overflow because every c(v, w) is at
 // most the degree of v, which the class bounds by 2^CW - 1.
-template <int CW>
+template <int CW, uint32_t WIN_WORDS>
 struct Ctr {
   static constexpr uint32_t PER = 32 / CW;
   static constexpr uint32_t MASK = (CW == 32) ? 0xFFFFFFFFu : ((1u << CW) - 1u);
-  static constexpr uint32_t Z = CT_WORDS * PER;
+  static constexpr uint32_t Z = WIN_WORDS * PER;
   __device__ static __forceinline__ void at(uint32_t idx, uint32_t &wi, uint32_t &sh) {
-    const uint32_t q = (PER == 1) ? 0u : idx / CT_WORDS;
-    wi = idx - q * CT_WORDS;
+    const uint32_t q = (PER == 1) ? 0u : idx / WIN_WORDS;
+    wi = idx - q * WIN_WORDS;
     sh = q * CW;
   }
   __device__ static __forceinline__ void inc(uint32_t *c, uint32_t idx) {
     uint32_t wi, sh;
     at(idx, wi, sh);
     atomicAdd(&c[wi], 1u << sh);
+  }
+  // increment and return the field's old value
+  __device__ static __forceinline__ uint32_t inc_get(uint32_t *c, uint32_t idx) {
+    uint32_t wi, sh;
+    at(idx, wi, sh);
+    return (atomicAdd(&c[wi], 1u << sh) >> sh) & MASK;
   }
   __device__ static __forceinline__ uint32_t take(uint32_t *c, uint32_t idx) {
     uint32_t wi, sh;
@@ -259,9 +294,13 @@ struct Ctr {
 // cur; four 32-element loads in flight per warp.  Targets are ascending, so the
 // in-window ones are a prefix.  On return cur is the first target >= hi (or
 // end) and nx that target's rank (INF_RANK at the end of the segment).
-template <int MODE, int CW>
+// Raising a counter from c to c + 1 adds exactly c new pairs (C(c+1, 2) -
+// C(c, 2) = c), so when ACC is set the old field values are summed into acc:
+// after the window acc holds sum_w C(c(v, w), 2) over its targets.
+template <int MODE, int CW, uint32_t WIN_WORDS, bool ACC>
 __device__ __forceinline__ void count_segment(const uint32_t *__restrict__ mR, uint32_t &cur, uint32_t end,
-                                              uint32_t lo, uint32_t hi, uint32_t r, uint32_t *ctr, uint32_t &nx) {
+                                              uint32_t lo, uint32_t hi, uint32_t r, uint32_t *ctr, uint32_t &nx,
+                                              uint64_t &acc) {
   const int lane = threadIdx.x & 31;
   while (true) {
     uint32_t w[4];
@@ -274,7 +313,10 @@ __device__ __forceinline__ void count_segment(const uint32_t *__restrict__ mR, u
     for (int k = 0; k < 4; k++) {
       const bool in = w[k] < hi;
       const uint32_t bal = __ballot_sync(0xffffffffu, in);
-      if (in && (MODE != MODE_SINGLE || w[k] != r)) Ctr<CW>::inc(ctr, w[k] - lo);
+      if (in && (!Full<MODE>::value || w[k] != r)) {
+        if (ACC) acc += Ctr<CW, WIN_WORDS>::inc_get(ctr, w[k] - lo);
+        else Ctr<CW, WIN_WORDS>::inc(ctr, w[k] - lo);
+      }
       const uint32_t n = __popc(bal);
       cur += n;
       if (n < 32) {
@@ -286,19 +328,30 @@ __device__ __forceinline__ void count_segment(const uint32_t *__restrict__ mR, u
   }
 }
 
-template <int MODE, int CW>
-__global__ void __launch_bounds__(CT_THREADS, 1) k_cta_win(WArgs a) {
+template <int MODE, int CW, int P>
+__global__ void __launch_bounds__(WinCfg<P>::THREADS, P) k_cta_win(WArgs a) {
+  constexpr int WIN_THREADS = WinCfg<P>::THREADS;
+  constexpr uint32_t WIN_WORDS = WinCfg<P>::WORDS;
+  constexpr uint32_t WIN_SMAX = WinCfg<P>::SMAX;
+  using C = Ctr<CW, WIN_WORDS>;
   extern __shared__ uint32_t sm[];
   uint32_t *ctr = sm;
-  uint32_t *s_cur = sm + CT_WORDS, *s_end = s_cur + SMAX, *s_ps = s_end + SMAX, *s_nx = s_ps + SMAX;
-  uint32_t *s_row = s_nx + SMAX;
-  __shared__ uint32_t sh_idx, sh_min, sh_carry;
-  __shared__ unsigned long long sh_acc, sh_win;
+  uint32_t *s_cur = sm + WIN_WORDS, *s_end = s_cur + WIN_SMAX, *s_ps = s_end + WIN_SMAX, *s_nx = s_ps + WIN_SMAX;
+  uint32_t *s_row = s_nx + WIN_SMAX;
+  // window state, double buffered by window parity so that a window needs
+  // two barriers: one after counting, one after clearing
+  __shared__ uint32_t sh_min[2], sh_q[2], sh_q2[2];
+  __shared__ unsigned long long sh_win[2];
+  __shared__ uint32_t sh_idx, sh_carry;
+  __shared__ unsigned long long sh_acc;
   __shared__ uint32_t wtot[32];
-  constexpr int NW = CT_THREADS / 32;
-  constexpr uint32_t Z = Ctr<CW>::Z;
+  constexpr int NW = WIN_THREADS / 32;
+  constexpr uint32_t Z = C::Z;
+  // B accumulates at increment time except in VERTEX mode, whose exchange
+  // needs each target's final count anyway (b_w += C(c, 2))
+  constexpr bool ACC = (MODE != MODE_VERTEX);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (uint32_t i = threadIdx.x; i < CT_WORDS; i += CT_THREADS) ctr[i] = 0;
+  for (uint32_t i = threadIdx.x; i < WIN_WORDS; i += WIN_THREADS) ctr[i] = 0;
   uint64_t localB = 0;
   __syncthreads();
   while (true) {
@@ -306,6 +359,8 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_win(WArgs a) {
       sh_idx = atomicAdd(a.queue, 1u);
       sh_carry = 0;
       sh_acc = 0;
+      sh_min[0] = INF_RANK; sh_q[0] = 0; sh_q2[0] = 0; sh_win[0] = 0;
+      sh_min[1] = INF_RANK; sh_q[1] = 0; sh_q2[1] = 0; sh_win[1] = 0;
     }
     __syncthreads();
     const uint32_t idx = sh_idx;
@@ -314,12 +369,12 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_win(WArgs a) {
     const uint32_t r = (MODE == MODE_SINGLE) ? a.item_rank[item] : item;
     const uint64_t rb = a.offR[r], re = a.offR[r + 1];
     // ---- segments of the vertex's wedge lists
-    for (uint64_t base = rb; base < re; base += CT_THREADS) {
+    for (uint64_t base = rb; base < re; base += WIN_THREADS) {
       const uint64_t j = base + threadIdx.x;
       uint32_t b = 0, e = 0, ns = 0;
       if (j < re) {
         const uint32_t x = a.sX[j];
-        b = (MODE == MODE_SINGLE) ? (uint32_t)a.offM[x] : a.sB[j];
+        b = Full<MODE>::value ? (uint32_t)a.offM[x] : a.sB[j];
         e = (uint32_t)a.offM[x + 1];
         ns = (e - b + SEG - 1) / SEG;
       }
@@ -335,7 +390,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_win(WArgs a) {
       const uint32_t first = wtot[warp] + incl - ns;
       for (uint32_t k = 0; k < ns; k++) {
         const uint32_t s = first + k;
-        if (s >= SMAX) { atomicOr(a.err, DERR_CAPACITY); break; }
+        if (s >= WIN_SMAX) { atomicOr(a.err, DERR_CAPACITY); break; }
         const uint32_t sb = b + k * SEG;
         s_cur[s] = sb;
         s_end[s] = min(e, sb + SEG);
@@ -345,100 +400,111 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_win(WArgs a) {
       }
       __syncthreads();
     }
-    const uint32_t nseg = min(sh_carry, SMAX);
-    uint32_t lo = (MODE == MODE_SINGLE) ? 0u : r + 1;
+    const uint32_t nseg = min(sh_carry, WIN_SMAX);
+    uint32_t lo = Full<MODE>::value ? 0u : r + 1;
     uint32_t hi = (uint32_t)umin64((uint64_t)a.nS, (uint64_t)lo + Z);
-    while (true) {
-      if (threadIdx.x == 0) {
-        sh_min = INF_RANK;
-        sh_win = 0;
-      }
-      __syncthreads();
-      // ---- count
+    uint64_t acc = 0;  // per thread, over the whole vertex
+    for (uint32_t par = 0;; par ^= 1) {
+      // ---- count: warps take segments from a shared queue
       uint32_t wcount = 0;
-      for (uint32_t s = warp; s < nseg; s += NW) {
+      while (true) {
+        uint32_t s = 0;
+        if (lane == 0) s = atomicAdd(&sh_q[par], 1u);
+        s = __shfl_sync(0xffffffffu, s, 0);
+        if (s >= nseg) break;
         uint32_t cur = s_cur[s], nx = s_nx[s];
         const uint32_t end = s_end[s], ps = cur;
-        if (cur < end && nx < hi) count_segment<MODE, CW>(a.mR, cur, end, lo, hi, r, ctr, nx);
+        if (cur < end && nx < hi) count_segment<MODE, CW, WIN_WORDS, ACC>(a.mR, cur, end, lo, hi, r, ctr, nx, acc);
         else if (cur >= end) nx = INF_RANK;
         if (lane == 0) {
           s_cur[s] = cur;
           s_ps[s] = ps;
           s_nx[s] = nx;
-          if (nx != INF_RANK) atomicMin(&sh_min, nx);
+          if (nx != INF_RANK) atomicMin(&sh_min[par], nx);
         }
         wcount += cur - ps;
       }
-      if (lane == 0 && wcount) atomicAdd(&sh_win, (unsigned long long)wcount);
+      if ((MODE == MODE_VERTEX || MODE == MODE_EDGE || (MODE == MODE_LOCAL && a.be)) && lane == 0 && wcount)
+        atomicAdd(&sh_win[par], (unsigned long long)wcount);
       __syncthreads();
-      const uint64_t win = sh_win;
+      // the other parity's state was last read before this barrier: reset it
+      if (threadIdx.x == 0) {
+        sh_min[par ^ 1] = INF_RANK;
+        sh_q[par ^ 1] = 0;
+        sh_q2[par ^ 1] = 0;
+        sh_win[par ^ 1] = 0;
+      }
+      const uint32_t nm = sh_min[par];
       // ---- VERTEX / EDGE: every wedge of the window reads its final count
-      if ((MODE == MODE_VERTEX || MODE == MODE_EDGE) && win) {
-        for (uint32_t s = warp; s < nseg; s += NW) {
-          const uint32_t ps = s_ps[s], pe = s_cur[s];
-          if (ps >= pe) continue;
-          uint64_t rowsum = 0;
-          for (uint32_t i = ps + lane; i < pe; i += 32) {
-            const uint32_t c = Ctr<CW>::peek(ctr, a.mR[i] - lo);
-            if (c > 1) {
-              rowsum += c - 1;
-              if (MODE == MODE_EDGE) atomicAdd(&a.be[a.mEid[i]], (unsigned long long)(c - 1));
+      if (MODE == MODE_VERTEX || MODE == MODE_EDGE || MODE == MODE_LOCAL) {
+        if (sh_win[par]) {
+          while (true) {
+            uint32_t s = 0;
+            if (lane == 0) s = atomicAdd(&sh_q2[par], 1u);
+            s = __shfl_sync(0xffffffffu, s, 0);
+            if (s >= nseg) break;
+            const uint32_t ps = s_ps[s], pe = s_cur[s];
+            if (ps >= pe) continue;
+            uint64_t rowsum = 0;
+            for (uint32_t i = ps + lane; i < pe; i += 32) {
+              const uint32_t c = C::peek(ctr, __ldg(&a.mR[i]) - lo);
+              if (c > 1) {
+                rowsum += c - 1;
+                if (MODE != MODE_LOCAL && a.be) atomicAdd(&a.be[a.mEid[i]], (unsigned long long)(c - 1));
+              }
+            }
+            rowsum = warp_sum_u64(rowsum);
+            if (lane == 0 && rowsum) {
+              const uint64_t j = rb + s_row[s];
+              if (a.be) atomicAdd(&a.be[a.sEid[j]], (unsigned long long)rowsum);
+              if (MODE == MODE_VERTEX) atomicAdd(&a.bM[a.sX[j]], (unsigned long long)rowsum);
             }
           }
-          rowsum = warp_sum_u64(rowsum);
-          if (lane == 0 && rowsum) {
-            const uint64_t j = rb + s_row[s];
-            if (MODE == MODE_EDGE) atomicAdd(&a.be[a.sEid[j]], (unsigned long long)rowsum);
-            else atomicAdd(&a.bM[a.sX[j]], (unsigned long long)rowsum);
+          __syncthreads();
+        }
+      }
+      // ---- clear the window (VERTEX: C(c, 2) once per distinct w as it clears)
+      if (MODE == MODE_VERTEX) {
+        if (threadIdx.x == 0) sh_q[par ^ 1] = 0;  // reused below as the exchange queue of this window
+        __syncthreads();
+        while (true) {
+          uint32_t s = 0;
+          if (lane == 0) s = atomicAdd(&sh_q[par ^ 1], 1u);
+          s = __shfl_sync(0xffffffffu, s, 0);
+          if (s >= nseg) break;
+          const uint32_t ps = s_ps[s], pe = s_cur[s];
+          for (uint32_t i = ps + lane; i < pe; i += 32) {
+            const uint32_t w = __ldg(&a.mR[i]);
+            const uint32_t c = C::take(ctr, w - lo);
+            if (c > 1) {
+              const uint64_t p = pairs_of(c);
+              acc += p;
+              atomicAdd(&a.bS[a.vert_of[w]], (unsigned long long)p);
+            }
           }
         }
         __syncthreads();
+        if (threadIdx.x == 0) sh_q[par ^ 1] = 0;
+      } else {
+        // every target of the window has been counted: zero the words in use
+        const uint32_t used = (uint32_t)umin64((uint64_t)WIN_WORDS, (uint64_t)(hi - lo));
+        uint4 *c4 = reinterpret_cast<uint4 *>(ctr);
+        const uint32_t n4 = (used + 3) / 4;
+        for (uint32_t i = threadIdx.x; i < n4; i += WIN_THREADS) c4[i] = make_uint4(0, 0, 0, 0);
       }
-      // ---- exchange: C(c, 2) once per distinct w, and clear
-      uint64_t acc = 0;
-      if (win >= DENSE_MIN) {
-        for (uint32_t wi = threadIdx.x; wi < CT_WORDS; wi += CT_THREADS) {
-          const uint32_t word = ctr[wi];
-          if (!word) continue;
-#pragma unroll
-          for (uint32_t q = 0; q < Ctr<CW>::PER; q++) {
-            const uint32_t c = (word >> (q * CW)) & Ctr<CW>::MASK;
-            if (c > 1) {
-              const uint64_t p = pairs_of(c);
-              acc += p;
-              if (MODE == MODE_VERTEX) atomicAdd(&a.bS[a.vert_of[lo + q * CT_WORDS + wi]], (unsigned long long)p);
-            }
-          }
-          ctr[wi] = 0;
-        }
-      } else if (win) {
-        for (uint32_t s = warp; s < nseg; s += NW) {
-          const uint32_t ps = s_ps[s], pe = s_cur[s];
-          for (uint32_t i = ps + lane; i < pe; i += 32) {
-            const uint32_t w = a.mR[i];
-            if (MODE == MODE_SINGLE && w == r) continue;
-            const uint32_t c = Ctr<CW>::take(ctr, w - lo);
-            if (c > 1) {
-              const uint64_t p = pairs_of(c);
-              acc += p;
-              if (MODE == MODE_VERTEX) atomicAdd(&a.bS[a.vert_of[w]], (unsigned long long)p);
-            }
-          }
-        }
-      }
-      acc = warp_sum_u64(acc);
-      if (lane == 0 && acc) atomicAdd(&sh_acc, (unsigned long long)acc);
-      __syncthreads();
-      const uint32_t nm = sh_min;
       __syncthreads();
       if (nm == INF_RANK) break;
       lo = nm;
       hi = (uint32_t)umin64((uint64_t)a.nS, (uint64_t)lo + Z);
     }
+    acc = warp_sum_u64(acc);
+    if (lane == 0 && acc) atomicAdd(&sh_acc, (unsigned long long)acc);
+    __syncthreads();
     if (threadIdx.x == 0) {
       localB += sh_acc;
       if (MODE == MODE_VERTEX && sh_acc) atomicAdd(&a.bS[a.vert_of[r]], sh_acc);
       if (MODE == MODE_SINGLE) a.bitem[item] = sh_acc;
+      if (MODE == MODE_LOCAL && a.bS) a.bS[a.vert_of[r]] = sh_acc;
     }
     __syncthreads();
   }
@@ -480,7 +546,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_big(WArgs a) {
       uint32_t b = 0, e = 0, ns = 0;
       if (j < re) {
         const uint32_t x = a.sX[j];
-        b = (MODE == MODE_SINGLE) ? (uint32_t)a.offM[x] : a.sB[j];
+        b = Full<MODE>::value ? (uint32_t)a.offM[x] : a.sB[j];
         e = (uint32_t)a.offM[x + 1];
         ns = (e - b + BIG_SEG - 1) / BIG_SEG;
       }
@@ -508,7 +574,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_big(WArgs a) {
       __syncthreads();
     }
     const uint32_t nseg = min(s_carry, a.seg_cap);
-    uint32_t lo = (MODE == MODE_SINGLE) ? 0u : r + 1;
+    uint32_t lo = Full<MODE>::value ? 0u : r + 1;
     uint32_t hi = (uint32_t)umin64((uint64_t)a.nS, (uint64_t)lo + BIG_Z);
     while (true) {
       for (uint32_t sidx = warp; sidx < nseg; sidx += NW) {
@@ -516,7 +582,10 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_big(WArgs a) {
         uint32_t pos = sg[2], end = sg[1], nxt = sg[4];
         uint32_t pstart = pos;
         if (pos < end && nxt < hi) {
-          count_segment<MODE, 32>(a.mR, pos, end, lo, hi, r, ctr, nxt);
+          {
+            uint64_t unused = 0;
+            count_segment<MODE, 32, BIG_Z, false>(a.mR, pos, end, lo, hi, r, ctr, nxt, unused);
+          }
           if (lane == 0) { sg[2] = pos; sg[3] = pstart; sg[4] = nxt; }
         } else {
           if (lane == 0) sg[3] = pos;
@@ -525,7 +594,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_big(WArgs a) {
         if (lane == 0 && nxt != INF_RANK) atomicMin(&s_next_min, nxt);
       }
       __syncthreads();
-      if (MODE == MODE_VERTEX || MODE == MODE_EDGE) {
+      if (MODE == MODE_VERTEX || MODE == MODE_EDGE || (MODE == MODE_LOCAL && a.be)) {
         for (uint32_t sidx = warp; sidx < nseg; sidx += NW) {
           uint32_t *sg = seg + (size_t)sidx * 5;
           uint32_t ps = sg[3], pe = sg[2];
@@ -536,13 +605,13 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_big(WArgs a) {
             uint32_t c = ctr[a.mR[i] - lo];
             if (c > 1) {
               rowsum += c - 1;
-              if (MODE == MODE_EDGE) atomicAdd(&a.be[a.mEid[i]], (unsigned long long)(c - 1));
+              if (MODE != MODE_LOCAL && a.be) atomicAdd(&a.be[a.mEid[i]], (unsigned long long)(c - 1));
             }
           }
           rowsum = warp_sum_u64(rowsum);
           if (lane == 0 && rowsum) {
-            if (MODE == MODE_EDGE) atomicAdd(&a.be[a.sEid[j]], (unsigned long long)rowsum);
-            else atomicAdd(&a.bM[a.sX[j]], (unsigned long long)rowsum);
+            if (a.be) atomicAdd(&a.be[a.sEid[j]], (unsigned long long)rowsum);
+            if (MODE == MODE_VERTEX) atomicAdd(&a.bM[a.sX[j]], (unsigned long long)rowsum);
           }
         }
         __syncthreads();
@@ -553,7 +622,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_big(WArgs a) {
         uint32_t ps = sg[3], pe = sg[2];
         for (uint32_t i = ps + lane; i < pe; i += 32) {
           uint32_t w = a.mR[i];
-          if (MODE == MODE_SINGLE && w == r) continue;
+          if (Full<MODE>::value && w == r) continue;
           uint32_t c = atomicExch(&ctr[w - lo], 0u);
           if (c > 1) {
             uint64_t p = pairs_of(c);
@@ -577,6 +646,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_big(WArgs a) {
       localB += s_acc;
       if (MODE == MODE_VERTEX && s_acc) atomicAdd(&a.bS[a.vert_of[r]], s_acc);
       if (MODE == MODE_SINGLE) a.bitem[item] = s_acc;
+      if (MODE == MODE_LOCAL && a.bS) a.bS[a.vert_of[r]] = s_acc;
     }
     __syncthreads();
   }
@@ -589,10 +659,17 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_big(WArgs a) {
 __device__ __forceinline__ uint32_t class_of(uint64_t d, uint64_t w) {
   if (d < 2 || w == 0) return CLS_SKIP;
   if (w <= WH_MAX_WORK) return CLS_WARP;
-  if (d + w / SEG + 1 > SMAX) return CLS_BIG;
-  if (d <= 255) return CLS_W8;
-  if (d <= 65535) return CLS_W16;
-  return CLS_W32;
+  const uint64_t segs = d + w / SEG + 1;
+  uint32_t base;
+  if (segs <= WinCfg<P_SMALL>::SMAX) base = CLS_S0;
+  else if (segs <= WinCfg<P_LARGE>::SMAX) base = CLS_L0;
+  else return CLS_BIG;
+  // counter width: every c(v, w) <= degree of v
+  if (d <= 3) return base + 0;
+  if (d <= 15) return base + 1;
+  if (d <= 255) return base + 2;
+  if (d <= 65535) return base + 3;
+  return base + 4;
 }
 
 __global__ void k_classify(const uint64_t *offR, const uint64_t *work, uint32_t nS, uint32_t *cls_of,
@@ -639,22 +716,23 @@ int plan_classify(bfc_graph *g, Plan &p, cudaStream_t s) {
   int rc = BFC_OK;
 #define PC_TRY(x) do { rc = (x); if (rc) { cleanup(); return rc; } } while (0)
   PC_TRY(dalloc(cls_of, (uint64_t)std::max<uint32_t>(nS, 1) * 4, s));
-  PC_TRY(dalloc(cnt, 256, s));
-  BFC_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, 256, s));
-  unsigned int *counts = ptr<unsigned int>(cnt);                                      // [0, 8)
-  unsigned int *cursor = counts + 8;                                                  // [8, 16)
-  unsigned long long *maxseg = reinterpret_cast<unsigned long long *>(counts + 16);  // 1
-  unsigned long long *sums = reinterpret_cast<unsigned long long *>(counts + 18);    // 2 N
+  PC_TRY(dalloc(cnt, 512, s));
+  BFC_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, 512, s));
+  static_assert(N <= 16, "class arrays below hold 16 entries");
+  unsigned int *counts = ptr<unsigned int>(cnt);                                      // [0, 16)
+  unsigned int *cursor = counts + 16;                                                 // [16, 32)
+  unsigned long long *maxseg = reinterpret_cast<unsigned long long *>(counts + 32);  // 1
+  unsigned long long *sums = reinterpret_cast<unsigned long long *>(counts + 34);    // 2 N (<= 32)
   k_classify<<<grid_for(nS, 256), 256, 0, s>>>(ptr<uint64_t>(p.offR), ptr<uint64_t>(p.work), nS,
                                               ptr<uint32_t>(cls_of), counts, maxseg, sums);
   count_launch();
-  unsigned int hc[8];
+  unsigned int hc[16];
   unsigned long long hmax = 0, hs[2 * N];
-  BFC_CUDA_TRY(cudaMemcpyAsync(hc, counts, 32, cudaMemcpyDeviceToHost, s));
+  BFC_CUDA_TRY(cudaMemcpyAsync(hc, counts, 64, cudaMemcpyDeviceToHost, s));
   BFC_CUDA_TRY(cudaMemcpyAsync(&hmax, maxseg, 8, cudaMemcpyDeviceToHost, s));
   BFC_CUDA_TRY(cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, s));
   BFC_CUDA_TRY(cudaStreamSynchronize(s));
-  unsigned int hb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  unsigned int hb[16] = {};
   for (int c = 0; c < N; c++) {
     p.cls_count[c] = hc[c];
     p.cls_begin[c] = (c == 0) ? 0 : p.cls_begin[c - 1] + p.cls_count[c - 1];
@@ -663,17 +741,17 @@ int plan_classify(bfc_graph *g, Plan &p, cudaStream_t s) {
     p.cls_rows[c] = hs[N + c];
   }
   p.big_seg_cap = (uint32_t)std::min<unsigned long long>(hmax, 0xFFFFFFFFull);
-  BFC_CUDA_TRY(cudaMemcpyAsync(counts, hb, 32, cudaMemcpyHostToDevice, s));
+  BFC_CUDA_TRY(cudaMemcpyAsync(counts, hb, 64, cudaMemcpyHostToDevice, s));
   k_scatter_class<<<grid_for(nS, 256), 256, 0, s>>>(ptr<uint32_t>(cls_of), nS, counts, cursor, ptr<uint32_t>(p.cls));
   count_launch();
   // heaviest first inside each window class (better load balance at the tail)
   uint32_t maxn = 0;
-  for (int c = CLS_W8; c < N; c++) maxn = std::max(maxn, p.cls_count[c]);
+  for (int c = CLS_S0; c < N; c++) maxn = std::max(maxn, p.cls_count[c]);
   if (maxn > 1) {
     PC_TRY(dalloc(k1, (uint64_t)maxn * 8, s));
     PC_TRY(dalloc(k2, (uint64_t)maxn * 8, s));
     PC_TRY(dalloc(v2, (uint64_t)maxn * 4, s));
-    for (int c = CLS_W8; c < N; c++) {
+    for (int c = CLS_S0; c < N; c++) {
       const uint32_t nc = p.cls_count[c];
       if (nc < 2) continue;
       uint32_t *list = ptr<uint32_t>(p.cls) + p.cls_begin[c];
@@ -704,9 +782,9 @@ static int sm_count() {
 }
 
 static const char *tag_of(int kind, int mode) {
-  static const char *tags[3][4] = {{"warp.total", "warp.vertex", "warp.edge", "warp.single"},
-                                   {"win.total", "win.vertex", "win.edge", "win.single"},
-                                   {"big.total", "big.vertex", "big.edge", "big.single"}};
+  static const char *tags[3][5] = {{"warp.total", "warp.vertex", "warp.edge", "warp.single", "warp.local"},
+                                   {"win.total", "win.vertex", "win.edge", "win.single", "win.local"},
+                                   {"big.total", "big.vertex", "big.edge", "big.single", "big.local"}};
   return tags[kind][mode];
 }
 
@@ -716,6 +794,7 @@ static int launch_lists(bfc_graph *g, WArgs a, const uint32_t *const *lists, con
                         cudaStream_t s) {
   const int sms = sm_count();
   unsigned int *queues = ptr<unsigned int>(g->acc) + 16;  // one counter per class
+  static_assert(64 + 4 * Plan::NCLS <= 256, "queues live in the 256-byte accumulator block");
   BFC_CUDA_TRY(cudaMemsetAsync(queues, 0, 4 * Plan::NCLS, s));
   if (counts[CLS_WARP]) {
     WArgs w = a;
@@ -733,19 +812,33 @@ static int launch_lists(bfc_graph *g, WArgs a, const uint32_t *const *lists, con
     BFC_LAUNCHED();
     profile_end(tag_of(0, MODE), s);
   }
-  const bool any_win = counts[CLS_W8] || counts[CLS_W16] || counts[CLS_W32];
+  bool any_win = false;
+  for (int c = CLS_S0; c < CLS_BIG; c++) any_win = any_win || counts[c];
   if (any_win) profile_begin(tag_of(1, MODE), s);
-  for (int c = CLS_W8; c <= CLS_W32; c++) {
+  for (int c = CLS_S0; c < CLS_BIG; c++) {
     if (!counts[c]) continue;
     WArgs w = a;
     w.list = lists[c];
     w.list_n = counts[c];
     w.queue = queues + c;
-    void (*kern)(WArgs) = (c == CLS_W8) ? k_cta_win<MODE, 8> : (c == CLS_W16) ? k_cta_win<MODE, 16>
-                                                                              : k_cta_win<MODE, 32>;
-    BFC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WIN_SMEM));
-    const unsigned grid = std::min<unsigned>((unsigned)sms, w.list_n);
-    kern<<<grid, CT_THREADS, WIN_SMEM, s>>>(w);
+    const bool small = c < CLS_L0;
+    const int cw = CW_OF[(c - CLS_S0) % 5];
+    void (*kern)(WArgs) = nullptr;
+    if (small) {
+      kern = cw == 2 ? k_cta_win<MODE, 2, P_SMALL> : cw == 4 ? k_cta_win<MODE, 4, P_SMALL>
+           : cw == 8 ? k_cta_win<MODE, 8, P_SMALL> : cw == 16 ? k_cta_win<MODE, 16, P_SMALL>
+                                                              : k_cta_win<MODE, 32, P_SMALL>;
+    } else {
+      kern = cw == 2 ? k_cta_win<MODE, 2, P_LARGE> : cw == 4 ? k_cta_win<MODE, 4, P_LARGE>
+           : cw == 8 ? k_cta_win<MODE, 8, P_LARGE> : cw == 16 ? k_cta_win<MODE, 16, P_LARGE>
+                                                              : k_cta_win<MODE, 32, P_LARGE>;
+    }
+    const int per_sm = small ? P_SMALL : P_LARGE;
+    const int threads = small ? WinCfg<P_SMALL>::THREADS : WinCfg<P_LARGE>::THREADS;
+    const size_t smem = small ? WinCfg<P_SMALL>::SMEM : WinCfg<P_LARGE>::SMEM;
+    BFC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const unsigned grid = std::min<unsigned>((unsigned)(sms * per_sm), w.list_n);
+    kern<<<grid, threads, smem, s>>>(w);
     BFC_LAUNCHED();
   }
   if (any_win) profile_end(tag_of(1, MODE), s);
@@ -803,7 +896,7 @@ __global__ void k_item_classify(const uint32_t *item_rank, uint32_t n, const uin
   uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t i = warp; i < n; i += nw) {
-    const uint32_t r = item_rank[i];
+    const uint32_t r = item_rank ? item_rank[i] : (uint32_t)i;
     const uint64_t b = offR[r], e = offR[r + 1];
     uint64_t w = 0;
     for (uint64_t j = b + lane; j < e; j += 32) {
@@ -816,7 +909,7 @@ __global__ void k_item_classify(const uint32_t *item_rank, uint32_t n, const uin
       const uint32_t c = class_of(d, w);
       cls_of[i] = c;
       atomicAdd(&counts[c], 1u);
-      out[i] = 0;
+      if (out) out[i] = 0;
       if (c == CLS_BIG) atomicMax(maxseg, (unsigned long long)(d + w / BIG_SEG + 1));
     }
   }
@@ -830,8 +923,12 @@ __global__ void k_item_scatter(const uint32_t *cls_of, uint32_t n, const unsigne
   }
 }
 
-int vbfc_batch(bfc_graph *g, Plan &p, const uint32_t *item_rank, uint32_t n_items, unsigned long long *out,
-               cudaStream_t s) {
+// Whole-row counting for a batch of start ranks (item_rank, or every rank when
+// null): SINGLE writes b of each item to out; LOCAL writes b_v to bS, the row
+// sums b_e to be, and adds 2B to d_B.
+static int full_rows_batch(bfc_graph *g, Plan &p, int mode, const uint32_t *item_rank, uint32_t n_items,
+                           unsigned long long *out, unsigned long long *d_B, unsigned long long *bS,
+                           unsigned long long *be, cudaStream_t s) {
   constexpr int N = Plan::NCLS;
   if (n_items == 0) return BFC_OK;
   DBuf cls_of, lists, cnt;
@@ -840,38 +937,81 @@ int vbfc_batch(bfc_graph *g, Plan &p, const uint32_t *item_rank, uint32_t n_item
 #define VB_TRY(x) do { rc = (x); if (rc) { cleanup(); return rc; } } while (0)
   VB_TRY(dalloc(cls_of, (uint64_t)n_items * 4, s));
   VB_TRY(dalloc(lists, (uint64_t)n_items * 4, s));
-  VB_TRY(dalloc(cnt, 128, s));
-  BFC_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, 128, s));
-  unsigned int *counts = ptr<unsigned int>(cnt);                                      // [0, 8)
-  unsigned int *begin = counts + 8;                                                   // [8, 16)
-  unsigned int *cursor = counts + 16;                                                 // [16, 24)
-  unsigned long long *maxseg = reinterpret_cast<unsigned long long *>(counts + 24);
+  VB_TRY(dalloc(cnt, 256, s));
+  BFC_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, 256, s));
+  static_assert(N <= 16, "class arrays below hold 16 entries");
+  unsigned int *counts = ptr<unsigned int>(cnt);                                      // [0, 16)
+  unsigned int *begin = counts + 16;                                                  // [16, 32)
+  unsigned int *cursor = counts + 32;                                                 // [32, 48)
+  unsigned long long *maxseg = reinterpret_cast<unsigned long long *>(counts + 48);
   k_item_classify<<<grid_for((uint64_t)n_items * 32, 256), 256, 0, s>>>(item_rank, n_items, ptr<uint64_t>(p.offR),
                                                                         ptr<uint32_t>(p.sX), p.offM,
                                                                         ptr<uint32_t>(cls_of), counts, maxseg, out);
   count_launch();
-  unsigned int hc[8];
+  unsigned int hc[16];
   unsigned long long hmax = 0;
-  BFC_CUDA_TRY(cudaMemcpyAsync(hc, counts, 32, cudaMemcpyDeviceToHost, s));
+  BFC_CUDA_TRY(cudaMemcpyAsync(hc, counts, 64, cudaMemcpyDeviceToHost, s));
   BFC_CUDA_TRY(cudaMemcpyAsync(&hmax, maxseg, 8, cudaMemcpyDeviceToHost, s));
   BFC_CUDA_TRY(cudaStreamSynchronize(s));
-  unsigned int hb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  unsigned int hb[16] = {};
   uint32_t run = 0;
   for (int c = 1; c < N; c++) { hb[c] = run; run += hc[c]; }
-  BFC_CUDA_TRY(cudaMemcpyAsync(begin, hb, 32, cudaMemcpyHostToDevice, s));
+  BFC_CUDA_TRY(cudaMemcpyAsync(begin, hb, 64, cudaMemcpyHostToDevice, s));
   k_item_scatter<<<grid_for(n_items, 256), 256, 0, s>>>(ptr<uint32_t>(cls_of), n_items, begin, cursor,
                                                        ptr<uint32_t>(lists));
   count_launch();
   WArgs a = args_of(g, p);
   a.item_rank = item_rank;
   a.bitem = out;
-  a.B = ptr<unsigned long long>(g->acc) + 1;  // not read back
+  a.B = d_B;
+  a.bS = bS;
+  a.be = be;
   const uint32_t *L[N];
   uint32_t C[N];
   for (int c = 0; c < N; c++) { L[c] = ptr<uint32_t>(lists) + hb[c]; C[c] = (c == 0) ? 0 : hc[c]; }
-  VB_TRY(launch_lists<MODE_SINGLE>(g, a, L, C, (uint32_t)std::min<unsigned long long>(hmax, 0xFFFFFFFFull), s));
+  const uint32_t cap = (uint32_t)std::min<unsigned long long>(hmax, 0xFFFFFFFFull);
+  if (mode == MODE_LOCAL) VB_TRY(launch_lists<MODE_LOCAL>(g, a, L, C, cap, s));
+  else VB_TRY(launch_lists<MODE_SINGLE>(g, a, L, C, cap, s));
   cleanup();
 #undef VB_TRY
+  return BFC_OK;
+}
+
+int vbfc_batch(bfc_graph *g, Plan &p, const uint32_t *item_rank, uint32_t n_items, unsigned long long *out,
+               cudaStream_t s) {
+  // B is not read back here: it lands in the second accumulator word
+  return full_rows_batch(g, p, MODE_SINGLE, item_rank, n_items, out, ptr<unsigned long long>(g->acc) + 1, nullptr,
+                         nullptr, s);
+}
+
+// b_x of a midpoint vertex: half the sum of b_e over its edges (each butterfly
+// through x contains two of x's edges)
+__global__ void k_mid_from_edges(const uint64_t *offM, uint32_t nM, const uint32_t *mEid,
+                                 const unsigned long long *be, unsigned long long *bM) {
+  const int lane = threadIdx.x & 31;
+  uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t x = warp; x < nM; x += nw) {
+    uint64_t t = 0;
+    for (uint64_t i = offM[x] + lane; i < offM[x + 1]; i += 32) t += be[mEid[i]];
+    t = warp_sum_u64(t);
+    if (lane == 0) bM[x] = t / 2;
+  }
+}
+
+int wedge_local(bfc_graph *g, Plan &p, unsigned long long *d_2B, uint64_t *bS, uint64_t *bM, uint64_t *be,
+                cudaStream_t s) {
+  if (bM && !be) return BFC_EINVAL;
+  if (bS) BFC_CUDA_TRY(cudaMemsetAsync(bS, 0, (uint64_t)p.nS * 8, s));
+  if (be && p.m) BFC_CUDA_TRY(cudaMemsetAsync(be, 0, p.m * 8, s));
+  BFC_TRY(full_rows_batch(g, p, MODE_LOCAL, nullptr, p.nS, nullptr, d_2B,
+                          reinterpret_cast<unsigned long long *>(bS), reinterpret_cast<unsigned long long *>(be), s));
+  if (bM) {
+    k_mid_from_edges<<<grid_for((uint64_t)p.nM * 32, 256), 256, 0, s>>>(
+        p.offM, p.nM, ptr<uint32_t>(p.mEid), reinterpret_cast<const unsigned long long *>(be),
+        reinterpret_cast<unsigned long long *>(bM));
+    BFC_LAUNCHED();
+  }
   return BFC_OK;
 }
 

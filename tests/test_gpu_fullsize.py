@@ -34,6 +34,8 @@ def test_identities_and_sampled_vertices(big):
     bU, bV, B2 = G.per_vertex()
     assert B2 == B
     bU, bV = u64(bU), u64(bV)
+    oU2, oV2, _ = G.per_vertex(whole_rows=True)
+    assert np.array_equal(u64(oU2), bU) and np.array_equal(u64(oV2), bV)
     assert int(bU.sum()) == 2 * B and int(bV.sum()) == 2 * B
     dU = np.bincount(g.u, minlength=g.nU)
     # sample: the 20 highest-degree vertices and 180 spread over the rest, each side
@@ -50,6 +52,11 @@ def test_per_edge_identities_and_samples(big):
     be, B3 = G.per_edge()
     assert B3 == B
     be = u64(be)
+    # the whole-row sweep and the combined call agree element by element
+    be2, _ = G.per_edge(whole_rows=True)
+    assert np.array_equal(u64(be2), be)
+    lU, lV, le, B4 = G.local_counts()
+    assert B4 == B and np.array_equal(u64(le), be)
     assert int(be.sum()) == 4 * B
     cu, cv = G.edges()
     cu = cu.cpu().numpy().astype(np.uint32)

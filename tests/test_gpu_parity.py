@@ -34,16 +34,24 @@ def check_all(bfc, u, v, nU, nV, per_edge=True, sides=(None, "U", "V")):
             assert B == oB, (side, B, oB)
             if side is None:
                 assert s == oside
-        bU, bV, B2 = G.per_vertex()
-        assert B2 == oB
         oU, oV = O.per_vertex(u, v, nU, nV)
-        assert np.array_equal(u64(bU), oU)
-        assert np.array_equal(u64(bV), oV)
+        for whole in (False, True):
+            bU, bV, B2 = G.per_vertex(whole_rows=whole)
+            assert B2 == oB
+            assert np.array_equal(u64(bU), oU)
+            assert np.array_equal(u64(bV), oV)
         if per_edge:
-            be, B3 = G.per_edge()
-            assert B3 == oB
             can = O.canonical_ids(u, v, nU, nV)
-            assert np.array_equal(u64(be)[can], O.per_edge(u, v, nU, nV))
+            oe = O.per_edge(u, v, nU, nV)
+            for whole in (False, True):
+                be, B3 = G.per_edge(whole_rows=whole)
+                assert B3 == oB
+                assert np.array_equal(u64(be)[can], oe)
+            for whole in (False, True):
+                lU, lV, le, B4 = G.local_counts(whole_rows=whole)
+                assert B4 == oB
+                assert np.array_equal(u64(lU), oU) and np.array_equal(u64(lV), oV)
+                assert np.array_equal(u64(le)[can], oe)
     return oB
 
 
