@@ -144,6 +144,8 @@ struct bfc_graph {
   uint32_t maxU = 0, maxV = 0;
   bfc::Plan plan[2];
   bfc::Scratch scr;
+  bfc::DBuf beM;               // u64[m]  per-edge partial sums in midpoint-row order
+  bfc::DBuf bSr;               // u64[nS] per-vertex partial sums in rank order
   bfc::DBuf err;               // u32 device error word
   bfc::DBuf acc;               // u64 accumulators (small)
   cudaStream_t last_stream = nullptr;

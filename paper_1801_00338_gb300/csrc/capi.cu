@@ -77,7 +77,8 @@ int bfc_graph_free(bfc_graph *g) {
     DBuf *bufs[] = {&p.vert_of, &p.rank_of, &p.offR, &p.sX, &p.sEid, &p.sB, &p.mR, &p.mEid, &p.work, &p.cls};
     for (DBuf *b : bufs) dfree(*b, s);
   }
-  DBuf *gb[] = {&g->offU, &g->nbrU, &g->offV, &g->nbrV, &g->eidV, &g->degU, &g->degV, &g->err, &g->acc, &g->scr.buf};
+  DBuf *gb[] = {&g->offU, &g->nbrU, &g->offV, &g->nbrV, &g->eidV, &g->degU, &g->degV, &g->err, &g->acc, &g->scr.buf,
+                &g->beM, &g->bSr};
   for (DBuf *b : gb) dfree(*b, s);
   cudaStreamSynchronize(s);
   delete g;

@@ -88,6 +88,10 @@ struct WArgs {
   unsigned int *queue;
   unsigned long long *B;
   unsigned long long *bS, *bM, *be;
+  // ordered VERTEX / EDGE modes: scattered updates go to these, then one pass
+  // moves them to bS (by vertex id) and be (by canonical edge id):
+  unsigned long long *beM;  // per midpoint-row entry: lanes of a warp hit consecutive words
+  unsigned long long *bSr;  // per start rank: the hot top ranks stay in L2
   uint32_t *err;
   // big class: segment scratch (per CTA, seg_cap entries each)
   uint32_t *seg;        // 5 u32 per segment: begin, end, cur, pstart, next
@@ -211,7 +215,7 @@ __global__ void __launch_bounds__(WH_WARPS * 32) k_warp_class(WArgs a) {
         uint32_t c = wh_lookup(keys, cnts, a.mR[i]);
         if (c > 1) {
           if (a.be) {
-            atomicAdd(&a.be[a.mEid[i]], (unsigned long long)(c - 1));
+            atomicAdd(&a.beM[i], (unsigned long long)(c - 1));
             atomicAdd(&a.be[a.sEid[j]], (unsigned long long)(c - 1));
           }
           if (MODE == MODE_VERTEX) atomicAdd(&a.bM[a.sX[j]], (unsigned long long)(c - 1));
@@ -233,7 +237,7 @@ __global__ void __launch_bounds__(WH_WARPS * 32) k_warp_class(WArgs a) {
       if (k != EMPTY_KEY) {
         uint64_t p = pairs_of(cnts[i]);
         acc += p;
-        if (MODE == MODE_VERTEX && p) atomicAdd(&a.bS[a.vert_of[k]], (unsigned long long)p);
+        if (MODE == MODE_VERTEX && p) atomicAdd(&a.bSr[k], (unsigned long long)p);
         keys[i] = EMPTY_KEY;
         cnts[i] = 0;
       }
@@ -241,7 +245,7 @@ __global__ void __launch_bounds__(WH_WARPS * 32) k_warp_class(WArgs a) {
     acc = warp_sum_u64(acc);
     if (lane == 0) {
       localB += acc;
-      if (MODE == MODE_VERTEX && acc) atomicAdd(&a.bS[a.vert_of[r]], (unsigned long long)acc);
+      if (MODE == MODE_VERTEX && acc) atomicAdd(&a.bSr[r], (unsigned long long)acc);
       if (MODE == MODE_SINGLE) a.bitem[item] = acc;
       if (MODE == MODE_LOCAL && a.bS) a.bS[a.vert_of[r]] = acc;
     }
@@ -450,7 +454,7 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, P) k_cta_win(WArgs a) {
               const uint32_t c = C::peek(ctr, __ldg(&a.mR[i]) - lo);
               if (c > 1) {
                 rowsum += c - 1;
-                if (MODE != MODE_LOCAL && a.be) atomicAdd(&a.be[a.mEid[i]], (unsigned long long)(c - 1));
+                if (MODE != MODE_LOCAL && a.be) atomicAdd(&a.beM[i], (unsigned long long)(c - 1));
               }
             }
             rowsum = warp_sum_u64(rowsum);
@@ -479,7 +483,7 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, P) k_cta_win(WArgs a) {
             if (c > 1) {
               const uint64_t p = pairs_of(c);
               acc += p;
-              atomicAdd(&a.bS[a.vert_of[w]], (unsigned long long)p);
+              atomicAdd(&a.bSr[w], (unsigned long long)p);
             }
           }
         }
@@ -502,7 +506,7 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, P) k_cta_win(WArgs a) {
     __syncthreads();
     if (threadIdx.x == 0) {
       localB += sh_acc;
-      if (MODE == MODE_VERTEX && sh_acc) atomicAdd(&a.bS[a.vert_of[r]], sh_acc);
+      if (MODE == MODE_VERTEX && sh_acc) atomicAdd(&a.bSr[r], sh_acc);
       if (MODE == MODE_SINGLE) a.bitem[item] = sh_acc;
       if (MODE == MODE_LOCAL && a.bS) a.bS[a.vert_of[r]] = sh_acc;
     }
@@ -605,7 +609,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_big(WArgs a) {
             uint32_t c = ctr[a.mR[i] - lo];
             if (c > 1) {
               rowsum += c - 1;
-              if (MODE != MODE_LOCAL && a.be) atomicAdd(&a.be[a.mEid[i]], (unsigned long long)(c - 1));
+              if (MODE != MODE_LOCAL && a.be) atomicAdd(&a.beM[i], (unsigned long long)(c - 1));
             }
           }
           rowsum = warp_sum_u64(rowsum);
@@ -627,7 +631,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_big(WArgs a) {
           if (c > 1) {
             uint64_t p = pairs_of(c);
             acc += p;
-            if (MODE == MODE_VERTEX) atomicAdd(&a.bS[a.vert_of[w]], (unsigned long long)p);
+            if (MODE == MODE_VERTEX) atomicAdd(&a.bSr[w], (unsigned long long)p);
           }
         }
       }
@@ -644,7 +648,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_big(WArgs a) {
     }
     if (threadIdx.x == 0) {
       localB += s_acc;
-      if (MODE == MODE_VERTEX && s_acc) atomicAdd(&a.bS[a.vert_of[r]], s_acc);
+      if (MODE == MODE_VERTEX && s_acc) atomicAdd(&a.bSr[r], s_acc);
       if (MODE == MODE_SINGLE) a.bitem[item] = s_acc;
       if (MODE == MODE_LOCAL && a.bS) a.bS[a.vert_of[r]] = s_acc;
     }
@@ -1015,6 +1019,19 @@ int wedge_local(bfc_graph *g, Plan &p, unsigned long long *d_2B, uint64_t *bS, u
   return BFC_OK;
 }
 
+// move the staged sums to their outputs: be[canonical id] += beM[row entry],
+// bS[vertex id] += bSr[rank]
+__global__ void k_finish_edges(const uint32_t *mEid, uint64_t m, const unsigned long long *beM,
+                               unsigned long long *be) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x)
+    be[mEid[i]] += beM[i];  // every canonical edge appears once in midpoint-row order
+}
+__global__ void k_finish_vertices(const uint32_t *vert_of, uint32_t nS, const unsigned long long *bSr,
+                                  unsigned long long *bS) {
+  for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nS; r += (uint64_t)gridDim.x * blockDim.x)
+    bS[vert_of[r]] += bSr[r];
+}
+
 int wedge_count(bfc_graph *g, Plan &p, Mode mode, unsigned long long *d_B, uint64_t *bS, uint64_t *bM, uint64_t *be,
                 cudaStream_t s) {
   WArgs a = args_of(g, p);
@@ -1022,12 +1039,33 @@ int wedge_count(bfc_graph *g, Plan &p, Mode mode, unsigned long long *d_B, uint6
   a.bS = reinterpret_cast<unsigned long long *>(bS);
   a.bM = reinterpret_cast<unsigned long long *>(bM);
   a.be = reinterpret_cast<unsigned long long *>(be);
-  switch (mode) {
-    case MODE_TOTAL: return launch_classes<MODE_TOTAL>(g, p, a, s);
-    case MODE_VERTEX: return launch_classes<MODE_VERTEX>(g, p, a, s);
-    case MODE_EDGE: return launch_classes<MODE_EDGE>(g, p, a, s);
-    default: return BFC_EINVAL;
+  if (be && p.m) {
+    BFC_TRY(dalloc(g->beM, p.m * 8, s));
+    BFC_CUDA_TRY(cudaMemsetAsync(g->beM.p, 0, p.m * 8, s));
+    a.beM = ptr<unsigned long long>(g->beM);
   }
+  if (bS && p.nS) {
+    BFC_TRY(dalloc(g->bSr, (uint64_t)p.nS * 8, s));
+    BFC_CUDA_TRY(cudaMemsetAsync(g->bSr.p, 0, (uint64_t)p.nS * 8, s));
+    a.bSr = ptr<unsigned long long>(g->bSr);
+  }
+  int rc = BFC_EINVAL;
+  switch (mode) {
+    case MODE_TOTAL: rc = launch_classes<MODE_TOTAL>(g, p, a, s); break;
+    case MODE_VERTEX: rc = launch_classes<MODE_VERTEX>(g, p, a, s); break;
+    case MODE_EDGE: rc = launch_classes<MODE_EDGE>(g, p, a, s); break;
+    default: break;
+  }
+  if (rc) return rc;
+  if (a.beM) {
+    k_finish_edges<<<grid_for(p.m, 256), 256, 0, s>>>(ptr<uint32_t>(p.mEid), p.m, a.beM, a.be);
+    BFC_LAUNCHED();
+  }
+  if (a.bSr) {
+    k_finish_vertices<<<grid_for(p.nS, 256), 256, 0, s>>>(ptr<uint32_t>(p.vert_of), p.nS, a.bSr, a.bS);
+    BFC_LAUNCHED();
+  }
+  return BFC_OK;
 }
 
 }  // namespace bfc
