@@ -204,6 +204,36 @@ int bfc_profile_enable(int on);
 int bfc_profile_reset(void);
 int bfc_profile_read(const char *tag, uint64_t *launches, double *total_ms);
 
+/* ---- allocation-free exact count (the paper has no counterpart) --------- */
+
+/* Size of the library-resident scratch array used by bfc_exact_csr_noalloc:
+ * 16,777,216 32-bit words (64 MiB), held by every GPU that loads the library
+ * until the process exits. */
+#define BFC_NOALLOC_SCRATCH_WORDS (16u * 1024u * 1024u)
+
+/* B(G) of a graph given as device CSR arrays, without allocating anything.
+ * For callers that cannot allocate device memory when they need the count:
+ * work recorded while a stream is being captured (cudaMalloc cannot be
+ * recorded into a graph), services whose device memory is reserved up front
+ * by another allocator or a fixed budget, and latency-bound loops that must
+ * not wait on the allocator.
+ *   offU : device, nU + 1 row offsets of the U rows;  nbrU : device, V ids
+ *   offV : device, nV + 1 row offsets of the V rows;  nbrV : device, U ids
+ *          (both sides describe the same simple graph; rows need not be sorted)
+ *   flags: BFC_SIDE_AUTO (Algorithm 1's choice) / BFC_SIDE_U / BFC_SIDE_V
+ *   out_B: device, one uint64, written in stream order (no host sync)
+ * The only working memory is a __device__ array of BFC_NOALLOC_SCRATCH_WORDS
+ * words inside this library; its device address is looked up (with
+ * cudaGetSymbolAddress) on the first call on each device, so make that first
+ * call before any stream capture.  Every call shares the array and clears the
+ * part it uses; calls that overlap on the GPU (different streams, no ordering
+ * between them) race on it and must be serialised by the caller.
+ * Errors: BFC_ERANGE if max(nU, nV) > BFC_NOALLOC_SCRATCH_WORDS - 64 or both
+ * are 0 (checked before any pointer is touched), BFC_EINVAL for bad flags or
+ * null pointers, BFC_ECUDA for a failed launch or symbol lookup. */
+int bfc_exact_csr_noalloc(const uint64_t *offU, const uint32_t *nbrU, uint32_t nU, const uint64_t *offV,
+                          const uint32_t *nbrV, uint32_t nV, uint32_t flags, uint64_t *out_B, void *stream);
+
 /* ---- misc -------------------------------------------------------------- */
 const char *bfc_strerror(int code);
 /* Number of kernel launches this library has made on the calling thread's

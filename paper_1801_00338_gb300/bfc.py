@@ -61,6 +61,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "bfc_vsamp": [P, u64, P, u32, u64, P, P, P, P],
         "bfc_proposal_from_weights": [P, P, u32, P, P],
         "bfc_proposal_free": [P],
+        "bfc_exact_csr_noalloc": [P, P, u32, P, P, u32, u32, P, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -279,6 +280,13 @@ def bfc_vsamp(h: int, k: int, trials: int, seed: int, proposal: int | None = Non
     if want_draws:
         return est, drawn[: trials * k], bd[: trials * k]
     return est
+
+
+def bfc_exact_csr_noalloc(offU, nbrU, nU: int, offV, nbrV, nV: int, out_B, flags: int = 0, stream=None) -> int:
+    """ExactBFC on device CSR tensors without allocating; out_B is a 1-element
+    int64 CUDA tensor that receives B in stream order.  Returns the status code."""
+    return int(load().bfc_exact_csr_noalloc(_dptr(offU), _dptr(nbrU), nU, _dptr(offV), _dptr(nbrV), nV, flags,
+                                            _dptr(out_B), _stream_ptr(stream)))
 
 
 # ----------------------------------------------------------------------------
