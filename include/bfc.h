@@ -137,6 +137,23 @@ int bfc_per_edge(bfc_graph *g, uint32_t flags, uint64_t *be, uint64_t *out_B, vo
 int bfc_local_counts(bfc_graph *g, uint32_t flags, uint64_t *bU, uint64_t *bV, uint64_t *be, uint64_t *out_B,
                      void *stream);
 
+/* ExactBFC (Algorithm 1) of G independent graphs in one pass.
+ *   u, v     : the graphs' edge lists one after another (host or device per
+ *              BFC_INPUT_DEVICE); graph g owns edges edge_off[g] .. edge_off[g+1]
+ *              and its ids are local: u < nU[g], v < nV[g]; no repeated edges.
+ *   edge_off : host, G + 1 entries, edge_off[0] = 0
+ *   nU, nV   : host, G entries each (all > 0)
+ *   B_out    : host, G entries: B of each graph
+ *   side_out : host, G entries (may be NULL): 0 if graph g started from U,
+ *              1 if from V (each graph gets Algorithm 1's own choice)
+ * A butterfly never spans two components, so the batch is counted as one
+ * disjoint union in which each graph's start side is placed on the union's U
+ * side; every start vertex's pair sum goes to its graph.
+ * Errors: BFC_EINVAL, BFC_ERANGE (an id outside its graph, or the union has
+ * 2^32 edges or vertices or more), BFC_EDUP, BFC_ENOMEM, BFC_ECUDA. */
+int bfc_exact_batch(const uint32_t *u, const uint32_t *v, const uint64_t *edge_off, const uint32_t *nU,
+                    const uint32_t *nV, uint32_t G, uint32_t flags, uint64_t *B_out, int *side_out, void *stream);
+
 /* ---- sparsification (Section 6) --------------------------------------- */
 
 /* ESpar (Algorithm 8), `trials` independent trials.  Trial t keeps canonical
@@ -233,6 +250,40 @@ int bfc_profile_read(const char *tag, uint64_t *launches, double *total_ms);
  * null pointers, BFC_ECUDA for a failed launch or symbol lookup. */
 int bfc_exact_csr_noalloc(const uint64_t *offU, const uint32_t *nbrU, uint32_t nU, const uint64_t *offV,
                           const uint32_t *nbrV, uint32_t nV, uint32_t flags, uint64_t *out_B, void *stream);
+
+/* ---- learned sampling proposal (an extension, not in the paper) --------- */
+/* A small network scores every vertex from cheap features; the scores become
+ * the weights of bfc_vsamp's mixture proposal.  Unbiasedness rests on the
+ * importance weights b / (4 q) of bfc_vsamp, not on the network.
+ * Layout of the parameter vector (BFC_MLP_PARAMS values): W1[6][64], b1[64],
+ * W2[64][64], b2[64], W3[64], b3; GELU (erf form) after each hidden layer;
+ * weights in bfloat16 (stored as uint16_t bits), fp32 accumulation. */
+#define BFC_MLP_FEATURES 6
+#define BFC_MLP_PARAMS 4673
+
+/* Per-vertex features, row-major float[nU + nV][6] (device), U rows first:
+ * log1p(d)/8, log1p(sum of neighbour degrees)/16, log1p(wedges ending at v)/16,
+ * log1p(wedges centred on v)/16, side (0 = U, 1 = V), log1p(max neighbour
+ * degree)/16.  O(m) work. */
+int bfc_features(bfc_graph *g, float *feat, void *stream);
+/* t[i] = log1p(b[i]) (device arrays of n), the regression target. */
+int bfc_mlp_targets(const uint64_t *b, uint64_t n, float *t, void *stream);
+/* y[i] = network(X[i]) for n rows (device). */
+int bfc_mlp_forward(const uint16_t *w_bf16, const float *X, uint64_t n, float *y, void *stream);
+/* grad (device, BFC_MLP_PARAMS floats, overwritten) = gradient of
+ * (1/n) sum_i (network(X[r_i]) - T[r_i])^2 over rows r_i = idx[i] (or i when
+ * idx is NULL); *loss (device, may be NULL) receives that mean. */
+int bfc_mlp_grad(const uint16_t *w_bf16, const float *X, const float *T, const uint32_t *idx, uint64_t n,
+                 float *grad, float *loss, void *stream);
+/* One Adam step (Kingma & Ba 2014) on the fp32 master weights w, refreshing
+ * their bfloat16 copy; step counts from 1. */
+int bfc_mlp_adam(float *w, uint16_t *w_bf16, float *m, float *v, const float *grad, uint32_t P, float lr,
+                 float beta1, float beta2, float eps, uint32_t step, void *stream);
+/* w_bf16[i] = round-to-nearest-even bfloat16 of w[i]. */
+int bfc_mlp_to_bf16(const float *w, uint16_t *w_bf16, uint32_t P, void *stream);
+/* A vsamp proposal from scores s (device, nU + nV floats): integer weights
+ * max(1, floor(2^24 exp(s_i - max s))), i.e. proportional to exp(s). */
+int bfc_proposal_from_scores(bfc_graph *g, const float *scores, void *stream, bfc_proposal **out);
 
 /* ---- misc -------------------------------------------------------------- */
 const char *bfc_strerror(int code);

@@ -62,6 +62,14 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "bfc_proposal_from_weights": [P, P, u32, P, P],
         "bfc_proposal_free": [P],
         "bfc_exact_csr_noalloc": [P, P, u32, P, P, u32, u32, P, P],
+        "bfc_exact_batch": [P, P, P, P, P, u32, u32, P, P, P],
+        "bfc_features": [P, P, P],
+        "bfc_mlp_targets": [P, u64, P, P],
+        "bfc_mlp_forward": [P, P, u64, P, P],
+        "bfc_mlp_grad": [P, P, P, P, u64, P, P, P],
+        "bfc_mlp_adam": [P, P, P, P, P, u32, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, u32, P],
+        "bfc_mlp_to_bf16": [P, P, u32, P],
+        "bfc_proposal_from_scores": [P, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -280,6 +288,82 @@ def bfc_vsamp(h: int, k: int, trials: int, seed: int, proposal: int | None = Non
     if want_draws:
         return est, drawn[: trials * k], bd[: trials * k]
     return est
+
+
+MLP_FEATURES = 6
+MLP_PARAMS = 4673
+
+
+def bfc_features(h: int, n: int, stream=None):
+    import torch
+    f = torch.empty((n, MLP_FEATURES), dtype=torch.float32, device="cuda")
+    _check(load().bfc_features(h, _dptr(f), _stream_ptr(stream)), "bfc_features")
+    return f
+
+
+def bfc_mlp_targets(b, stream=None):
+    import torch
+    t = torch.empty(b.numel(), dtype=torch.float32, device="cuda")
+    _check(load().bfc_mlp_targets(_dptr(b), b.numel(), _dptr(t), _stream_ptr(stream)), "bfc_mlp_targets")
+    return t
+
+
+def bfc_mlp_forward(w_bf16, X, stream=None):
+    import torch
+    y = torch.empty(X.shape[0], dtype=torch.float32, device="cuda")
+    _check(load().bfc_mlp_forward(_dptr(w_bf16), _dptr(X), X.shape[0], _dptr(y), _stream_ptr(stream)),
+           "bfc_mlp_forward")
+    return y
+
+
+def bfc_mlp_grad(w_bf16, X, T, idx=None, n=None, stream=None):
+    import torch
+    grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    n = (idx.numel() if idx is not None else X.shape[0]) if n is None else n
+    _check(load().bfc_mlp_grad(_dptr(w_bf16), _dptr(X), _dptr(T), _dptr(idx) if idx is not None else None, n,
+                               _dptr(grad), _dptr(loss), _stream_ptr(stream)), "bfc_mlp_grad")
+    return grad, loss
+
+
+def bfc_mlp_adam(w, w_bf16, m, v, grad, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(load().bfc_mlp_adam(_dptr(w), _dptr(w_bf16), _dptr(m), _dptr(v), _dptr(grad), MLP_PARAMS, lr, beta1, beta2,
+                               eps, step, _stream_ptr(stream)), "bfc_mlp_adam")
+
+
+def bfc_mlp_to_bf16(w, stream=None):
+    import torch
+    wb = torch.empty(MLP_PARAMS, dtype=torch.int16, device="cuda")
+    _check(load().bfc_mlp_to_bf16(_dptr(w), _dptr(wb), MLP_PARAMS, _stream_ptr(stream)), "bfc_mlp_to_bf16")
+    return wb
+
+
+def bfc_proposal_from_scores(h: int, scores, stream=None) -> int:
+    p = ctypes.c_void_p()
+    _check(load().bfc_proposal_from_scores(h, _dptr(scores), _stream_ptr(stream), ctypes.byref(p)),
+           "bfc_proposal_from_scores")
+    return p.value
+
+
+def bfc_exact_batch(graphs, stream=None):
+    """B of every graph in a list of (u, v, nU, nV) host edge lists, in one pass.
+
+    Returns (B array, start side array)."""
+    G = len(graphs)
+    sizes = [len(g[0]) for g in graphs]
+    eoff = np.zeros(G + 1, np.uint64)
+    np.cumsum(sizes, out=eoff[1:])
+    u = np.ascontiguousarray(np.concatenate([np.asarray(g[0], np.uint32) for g in graphs]) if G else
+                             np.zeros(0, np.uint32))
+    v = np.ascontiguousarray(np.concatenate([np.asarray(g[1], np.uint32) for g in graphs]) if G else
+                             np.zeros(0, np.uint32))
+    nU = np.array([g[2] for g in graphs], np.uint32)
+    nV = np.array([g[3] for g in graphs], np.uint32)
+    B = np.zeros(G, np.uint64)
+    side = np.zeros(G, np.int32)
+    _check(load().bfc_exact_batch(u.ctypes.data, v.ctypes.data, eoff.ctypes.data, nU.ctypes.data, nV.ctypes.data, G,
+                                  0, B.ctypes.data, side.ctypes.data, _stream_ptr(stream)), "bfc_exact_batch")
+    return B, side
 
 
 def bfc_exact_csr_noalloc(offU, nbrU, nU: int, offV, nbrV, nV: int, out_B, flags: int = 0, stream=None) -> int:

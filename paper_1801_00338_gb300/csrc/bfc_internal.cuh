@@ -164,6 +164,10 @@ enum Mode { MODE_TOTAL = 0, MODE_VERTEX = 1, MODE_EDGE = 2, MODE_SINGLE = 3, MOD
 // ids) or null; be: per-edge output (canonical ids) or null.
 int wedge_count(bfc_graph *g, Plan &p, Mode mode, unsigned long long *d_B, uint64_t *bS, uint64_t *bM,
                 uint64_t *be, cudaStream_t s);
+// TOTAL mode on a disjoint union: also adds each start vertex's pair sum to
+// gB[grp_of_rank[rank]].
+int wedge_count_groups(bfc_graph *g, Plan &p, const uint32_t *grp_of_rank, unsigned long long *gB,
+                       unsigned long long *d_B, cudaStream_t s);
 int plan_classify(bfc_graph *g, Plan &p, cudaStream_t s);
 void plan_free(Plan &p, cudaStream_t s);
 // Algorithm 2 for a batch of start ranks of plan p: out[i] = b of the vertex

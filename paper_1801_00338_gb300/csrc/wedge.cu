@@ -100,6 +100,10 @@ struct WArgs {
   // MODE_SINGLE (Algorithm 2 on a batch): list holds item ids
   const uint32_t *item_rank;
   unsigned long long *bitem;
+  // TOTAL mode over a disjoint union of graphs: each start vertex's pair sum
+  // also goes to gB[grp[rank]] (its graph's count)
+  const uint32_t *grp;
+  unsigned long long *gB;
 };
 
 __device__ __forceinline__ uint64_t umin64(uint64_t x, uint64_t y) { return x < y ? x : y; }
@@ -248,6 +252,7 @@ __global__ void __launch_bounds__(WH_WARPS * 32) k_warp_class(WArgs a) {
       if (MODE == MODE_VERTEX && acc) atomicAdd(&a.bSr[r], (unsigned long long)acc);
       if (MODE == MODE_SINGLE) a.bitem[item] = acc;
       if (MODE == MODE_LOCAL && a.bS) a.bS[a.vert_of[r]] = acc;
+      if (MODE == MODE_TOTAL && a.gB && acc) atomicAdd(&a.gB[a.grp[r]], (unsigned long long)acc);
     }
     __syncwarp();
   }
@@ -509,6 +514,7 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, P) k_cta_win(WArgs a) {
       if (MODE == MODE_VERTEX && sh_acc) atomicAdd(&a.bSr[r], sh_acc);
       if (MODE == MODE_SINGLE) a.bitem[item] = sh_acc;
       if (MODE == MODE_LOCAL && a.bS) a.bS[a.vert_of[r]] = sh_acc;
+      if (MODE == MODE_TOTAL && a.gB && sh_acc) atomicAdd(&a.gB[a.grp[r]], sh_acc);
     }
     __syncthreads();
   }
@@ -651,6 +657,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_big(WArgs a) {
       if (MODE == MODE_VERTEX && s_acc) atomicAdd(&a.bSr[r], s_acc);
       if (MODE == MODE_SINGLE) a.bitem[item] = s_acc;
       if (MODE == MODE_LOCAL && a.bS) a.bS[a.vert_of[r]] = s_acc;
+      if (MODE == MODE_TOTAL && a.gB && s_acc) atomicAdd(&a.gB[a.grp[r]], s_acc);
     }
     __syncthreads();
   }
@@ -1030,6 +1037,15 @@ __global__ void k_finish_vertices(const uint32_t *vert_of, uint32_t nS, const un
                                   unsigned long long *bS) {
   for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nS; r += (uint64_t)gridDim.x * blockDim.x)
     bS[vert_of[r]] += bSr[r];
+}
+
+int wedge_count_groups(bfc_graph *g, Plan &p, const uint32_t *grp_of_rank, unsigned long long *gB,
+                       unsigned long long *d_B, cudaStream_t s) {
+  WArgs a = args_of(g, p);
+  a.B = d_B;
+  a.grp = grp_of_rank;
+  a.gB = gB;
+  return launch_classes<MODE_TOTAL>(g, p, a, s);
 }
 
 int wedge_count(bfc_graph *g, Plan &p, Mode mode, unsigned long long *d_B, uint64_t *bS, uint64_t *bM, uint64_t *be,

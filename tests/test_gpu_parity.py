@@ -226,3 +226,18 @@ def test_vsamp_on_multi_window_graph(bfc):
     """Draws that land on CTA-class vertices walk every rank window (whole midpoint rows)."""
     g = synth.chung_lu_scaled(120_000, 30_000, 600_000, 2.1, 2.5, 31)
     _vsamp_check(bfc, g, 64, 2, 3)
+
+
+def test_batched_uneven_graphs_match_oracle(bfc):
+    """Many graphs of uneven size and skew in one pass; each graph's B and start side."""
+    params = synth.uneven_batch_params(48, 17, m_lo=50, m_hi=30_000)
+    graphs = []
+    for i, (nU, nV, m, gamma) in enumerate(params):
+        u, v = synth.chung_lu_bipartite(nU, nV, m, gamma, gamma, 300 + i)
+        graphs.append((u, v, nU, nV))
+    graphs.append(tuple(list(synth.complete_bipartite(30, 4)) + [30, 4]))   # starts from V
+    graphs.append((np.zeros(0, np.uint32), np.zeros(0, np.uint32), 3, 5))   # no edges
+    B, side = bfc.bfc_exact_batch(graphs)
+    for (u, v, nU, nV), b, sd in zip(graphs, B, side):
+        ob, os_ = O.exact(u, v, nU, nV)
+        assert int(b) == ob and int(sd) == os_
