@@ -1,0 +1,159 @@
+"""The learned VSamp proposal: training on exact per-vertex counts and use.
+
+An extension, not in the paper.  Algorithm 4 (VSamp) draws vertices
+uniformly and returns b_v * n / 4; Lemma 4 shows the estimate is unbiased but
+its variance grows with the spread of b_v.  Drawing v with probability q(v)
+and returning b_v / (4 q(v)) is unbiased for any q > 0 and has zero variance
+when q is proportional to b_v.  Here q mixes half uniform with half
+proportional to exp(s_v), where s_v is a small network's guess of log1p(b_v)
+from six cheap features; the uniform half keeps q >= 1/(2n), so the weights
+stay bounded and the estimator unbiased whatever the network predicts.
+
+Every numeric step runs in libbfc.so (features, forward, gradient, Adam,
+proposal weights, sampling); this module only orchestrates: it draws the
+training graphs, forms mini-batches and records timings.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import bfc, synth
+
+F, H = bfc.MLP_FEATURES, 64
+
+
+# parameter vector offsets: W1[6][64], b1[64], W2[64][64], b2[64], W3[64], b3
+OFF_W1, OFF_B1 = 0, F * H
+OFF_W2 = OFF_B1 + H
+OFF_B2 = OFF_W2 + H * H
+OFF_W3 = OFF_B2 + H
+OFF_B3 = OFF_W3 + H
+
+
+def init_params(seed: int, out_bias: float = 0.0) -> np.ndarray:
+    """Uniform Glorot initialisation of the weight matrices; zero hidden biases;
+    the output bias starts at `out_bias` (e.g. the mean target)."""
+    rng = np.random.default_rng(seed)
+    p = np.zeros(bfc.MLP_PARAMS, np.float32)
+    p[OFF_W1:OFF_B1] = rng.uniform(-1, 1, F * H) * math.sqrt(6.0 / (F + H))
+    p[OFF_W2:OFF_B2] = rng.uniform(-1, 1, H * H) * math.sqrt(6.0 / (H + H))
+    p[OFF_W3:OFF_B3] = rng.uniform(-1, 1, H) * math.sqrt(6.0 / (H + 1))
+    p[OFF_B3] = out_bias
+    return p
+
+
+def training_graph_params(count: int, seed: int, m_lo: float, m_hi: float):
+    """(nU, nV, m, gamma_u, gamma_v) per training graph: m log-uniform in
+    [m_lo, m_hi], exponents uniform in [1.9, 2.8], |V| = 2 |U|, mean degree 20 on U."""
+    r = synth.uniform01(seed, 0, 3 * count).reshape(count, 3)
+    out = []
+    for i in range(count):
+        m = int(round(math.exp(math.log(m_lo) + r[i, 0] * (math.log(m_hi) - math.log(m_lo)))))
+        nU = max(50, m // 20)
+        nV = 2 * nU
+        out.append((nU, nV, m, 1.9 + 0.9 * r[i, 1], 1.9 + 0.9 * r[i, 2]))
+    return out
+
+
+@dataclass
+class Dataset:
+    X: object = None      # torch float32 [n, 6] on the device
+    T: object = None      # torch float32 [n]
+    sizes: list = field(default_factory=list)
+
+
+def dataset_from_graphs(graphs) -> Dataset:
+    """Features and log1p(b) targets of every vertex of every graph (exact b from vBFC)."""
+    import torch
+    Xs, Ts, sizes = [], [], []
+    for u, v, nU, nV in graphs:
+        with bfc.Graph(u, v, nU, nV) as G:
+            X = bfc.bfc_features(G.h, nU + nV)
+            bU, bV, _ = G.per_vertex()
+            T = bfc.bfc_mlp_targets(torch.cat([bU, bV]))
+        Xs.append(X)
+        Ts.append(T)
+        sizes.append(nU + nV)
+    return Dataset(torch.cat(Xs), torch.cat(Ts), sizes)
+
+
+class Trainer:
+    """Adam on the fp32 master weights; the bf16 copy feeds the kernels."""
+
+    def __init__(self, seed: int = 0, lr: float = 1e-3, out_bias: float = 0.0):
+        import torch
+        self.w = torch.from_numpy(init_params(seed, out_bias)).cuda()
+        self.wb = bfc.bfc_mlp_to_bf16(self.w)
+        self.m = torch.zeros_like(self.w)
+        self.v = torch.zeros_like(self.w)
+        self.lr = lr
+        self.step = 0
+        self.history = []
+
+    def fit(self, data: Dataset, steps: int, batch: int = 65536, seed: int = 1, log_every: int = 50):
+        import torch
+        n = data.X.shape[0]
+        rng = np.random.default_rng(seed)
+        for s in range(steps):
+            idx = torch.from_numpy(rng.integers(0, n, min(batch, n), dtype=np.int64).astype(np.int32)).cuda()
+            grad, loss = bfc.bfc_mlp_grad(self.wb, data.X, data.T, idx)
+            self.step += 1
+            bfc.bfc_mlp_adam(self.w, self.wb, self.m, self.v, grad, self.lr, self.step)
+            if s % log_every == 0 or s == steps - 1:
+                self.history.append((self.step, float(loss.item())))
+        return self.history
+
+    def mse(self, data: Dataset) -> float:
+        y = bfc.bfc_mlp_forward(self.wb, data.X)
+        return float(((y - data.T) ** 2).mean().item())
+
+
+def scores(G: "bfc.Graph", wb):
+    """Network scores of every vertex of G (U first)."""
+    X = bfc.bfc_features(G.h, G.nU + G.nV)
+    return bfc.bfc_mlp_forward(wb, X)
+
+
+def proposal(G: "bfc.Graph", wb) -> int:
+    """A bfc_vsamp proposal handle built from the network's scores."""
+    return bfc.bfc_proposal_from_scores(G.h, scores(G, wb))
+
+
+def mixture_q_from_scores(s: np.ndarray) -> np.ndarray:
+    """q of the mixture for the integer weights the library derives from scores
+    (evaluation helper, float64 on the host)."""
+    s = np.asarray(s, dtype=np.float64)
+    w = np.maximum(1.0, np.floor(np.minimum(np.exp(np.minimum(s - s.max(), 0.0)) * 16777216.0, 16777216.0)))
+    n = s.size
+    return 0.5 / n + 0.5 * w / w.sum()
+
+
+def single_draw_variance(b: np.ndarray, q: np.ndarray | None = None) -> float:
+    """Exact variance of one draw b_v / (4 q(v)): sum_v b_v^2 / (16 q(v)) - B^2."""
+    b = np.asarray(b, dtype=np.float64)
+    if q is None:
+        q = np.full(b.size, 1.0 / b.size)
+    B = b.sum() / 4.0
+    return float(np.sum(b * b / (16.0 * q)) - B * B)
+
+
+def draws_for_median_error(var1: float, B: float, rel: float = 0.01) -> int:
+    """Draws k at which the median |estimate - B| / B of a k-draw mean is `rel`
+    (normal approximation: median |N(0, s^2)| = 0.6745 s)."""
+    return max(1, int(math.ceil((0.6744897501960817 / rel) ** 2 * var1 / (B * B))))
+
+
+def time_vsamp(G: "bfc.Graph", k: int, trials: int, seed: int, prop=None, reps: int = 3) -> float:
+    """Mean GPU wall time (s) of one bfc_vsamp call of `trials` x `k` draws."""
+    import torch
+    G.vsamp(k, trials, seed, proposal=prop)  # warm up (layouts of both sides)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r in range(reps):
+        G.vsamp(k, trials, seed + 1 + r, proposal=prop)
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t0) / reps
