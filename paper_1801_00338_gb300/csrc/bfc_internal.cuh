@@ -169,6 +169,12 @@ int wedge_count(bfc_graph *g, Plan &p, Mode mode, unsigned long long *d_B, uint6
 int wedge_count_groups(bfc_graph *g, Plan &p, const uint32_t *grp_of_rank, unsigned long long *gB,
                        unsigned long long *d_B, cudaStream_t s);
 int plan_classify(bfc_graph *g, Plan &p, cudaStream_t s);
+// The same classification with counts, offsets and lists left on the device
+// (dev: 48 words; sums: 2 NCLS + 1 u64 of scratch), and TOTAL counting that
+// reads them there: no host round trip, so both can be recorded in a graph.
+int plan_classify_device(Plan &p, uint32_t *cls_of, unsigned int *dev, unsigned long long *sums, cudaStream_t s);
+int wedge_count_device_lists(bfc_graph *g, Plan &p, const unsigned int *dev, uint32_t big_cap,
+                             unsigned long long *d_B, cudaStream_t s);
 void plan_free(Plan &p, cudaStream_t s);
 // Algorithm 2 for a batch of start ranks of plan p: out[i] = b of the vertex
 // at rank item_rank[i] (every other start vertex w != v, full midpoint rows).
@@ -179,7 +185,4 @@ int vbfc_batch(bfc_graph *g, Plan &p, const uint32_t *item_rank, uint32_t n_item
 // midpoint side from be (needs be), and d_2B += 2B (Lemma 1, Eq. (1)).
 int wedge_local(bfc_graph *g, Plan &p, unsigned long long *d_2B, uint64_t *bS, uint64_t *bM, uint64_t *be,
                 cudaStream_t s);
-// Filter plan `parent` to the canonical edges with keep[e] != 0 into `out`
-// (same start side and rank order; rows stay sorted).
-int plan_filter(bfc_graph *g, const Plan &parent, const uint32_t *keep, Plan &out, cudaStream_t s);
 }  // namespace bfc

@@ -104,7 +104,20 @@ struct WArgs {
   // also goes to gB[grp[rank]] (its graph's count)
   const uint32_t *grp;
   unsigned long long *gB;
+  // class lists whose lengths live on the device (launches recorded before
+  // the counts are known): list = dev_lists + dev_begin[cls], list_n = dev_count[cls]
+  const uint32_t *dev_lists;
+  const unsigned int *dev_begin, *dev_count;
+  uint32_t cls;
 };
+
+// resolve the vertex list of a launch (host-known or device-resident)
+__device__ __forceinline__ void resolve_list(WArgs &a) {
+  if (a.dev_count) {
+    a.list = a.dev_lists + a.dev_begin[a.cls];
+    a.list_n = a.dev_count[a.cls];
+  }
+}
 
 __device__ __forceinline__ uint64_t umin64(uint64_t x, uint64_t y) { return x < y ? x : y; }
 // modes that walk whole midpoint rows (every w != v) rather than the part after v
@@ -194,6 +207,7 @@ __device__ __forceinline__ void warp_for_each_wedge(const WArgs &a, uint64_t rb,
 template <int MODE>
 __global__ void __launch_bounds__(WH_WARPS * 32) k_warp_class(WArgs a) {
   extern __shared__ uint32_t smem[];
+  resolve_list(a);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t *keys = smem + (size_t)warp * 2 * WH_SLOTS;
   uint32_t *cnts = keys + WH_SLOTS;
@@ -343,6 +357,7 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, P) k_cta_win(WArgs a) {
   constexpr uint32_t WIN_WORDS = WinCfg<P>::WORDS;
   constexpr uint32_t WIN_SMAX = WinCfg<P>::SMAX;
   using C = Ctr<CW, WIN_WORDS>;
+  resolve_list(a);
   extern __shared__ uint32_t sm[];
   uint32_t *ctr = sm;
   uint32_t *s_cur = sm + WIN_WORDS, *s_end = s_cur + WIN_SMAX, *s_ps = s_end + WIN_SMAX, *s_nx = s_ps + WIN_SMAX;
@@ -527,6 +542,7 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, P) k_cta_win(WArgs a) {
 // ---------------------------------------------------------------------------
 template <int MODE>
 __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_big(WArgs a) {
+  resolve_list(a);
   extern __shared__ uint32_t ctr[];  // BIG_Z counters
   __shared__ uint32_t s_idx, s_next_min, s_carry;
   __shared__ unsigned long long s_acc;
@@ -799,39 +815,50 @@ static const char *tag_of(int kind, int mode) {
   return tags[kind][mode];
 }
 
-// class lists: lists[c], counts[c] for c in [0, NCLS)
+// class lists: lists[c], counts[c] for c in [0, NCLS).  With counts == null
+// the lists and their lengths are on the device (a.dev_*): every non-skip class
+// is launched with a full persistent grid and reads its length at start.
 template <int MODE>
 static int launch_lists(bfc_graph *g, WArgs a, const uint32_t *const *lists, const uint32_t *counts, uint32_t big_cap,
                         cudaStream_t s) {
   const int sms = sm_count();
+  const bool dev = counts == nullptr;
   unsigned int *queues = ptr<unsigned int>(g->acc) + 16;  // one counter per class
   static_assert(64 + 4 * Plan::NCLS <= 256, "queues live in the 256-byte accumulator block");
   BFC_CUDA_TRY(cudaMemsetAsync(queues, 0, 4 * Plan::NCLS, s));
-  if (counts[CLS_WARP]) {
+  auto have = [&](int c) { return dev || counts[c] != 0; };
+  auto setup = [&](WArgs &w, int c) {
+    w.cls = (uint32_t)c;
+    w.queue = queues + c;
+    if (!dev) {
+      w.list = lists[c];
+      w.list_n = counts[c];
+    }
+  };
+  auto cap = [&](unsigned full, int c) -> unsigned {
+    return dev ? full : std::max(1u, std::min<unsigned>(full, counts[c]));
+  };
+  if (have(CLS_WARP)) {
     WArgs w = a;
-    w.list = lists[CLS_WARP];
-    w.list_n = counts[CLS_WARP];
-    w.queue = queues + CLS_WARP;
+    setup(w, CLS_WARP);
     const size_t smem = (size_t)WH_WARPS * 2 * WH_SLOTS * 4;
     BFC_CUDA_TRY(cudaFuncSetAttribute(k_warp_class<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
     BFC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_warp_class<MODE>, WH_WARPS * 32, smem));
-    unsigned grid = (unsigned)std::max(1, occ) * sms;
-    grid = std::min<unsigned>(grid, (w.list_n + WH_WARPS - 1) / WH_WARPS);
+    const unsigned full = (unsigned)std::max(1, occ) * sms;
+    const unsigned grid = dev ? full : std::min<unsigned>(full, (counts[CLS_WARP] + WH_WARPS - 1) / WH_WARPS);
     profile_begin(tag_of(0, MODE), s);
     k_warp_class<MODE><<<grid, WH_WARPS * 32, smem, s>>>(w);
     BFC_LAUNCHED();
     profile_end(tag_of(0, MODE), s);
   }
   bool any_win = false;
-  for (int c = CLS_S0; c < CLS_BIG; c++) any_win = any_win || counts[c];
+  for (int c = CLS_S0; c < CLS_BIG; c++) any_win = any_win || have(c);
   if (any_win) profile_begin(tag_of(1, MODE), s);
   for (int c = CLS_S0; c < CLS_BIG; c++) {
-    if (!counts[c]) continue;
+    if (!have(c)) continue;
     WArgs w = a;
-    w.list = lists[c];
-    w.list_n = counts[c];
-    w.queue = queues + c;
+    setup(w, c);
     const bool small = c < CLS_L0;
     const int cw = CW_OF[(c - CLS_S0) % 5];
     void (*kern)(WArgs) = nullptr;
@@ -848,20 +875,17 @@ static int launch_lists(bfc_graph *g, WArgs a, const uint32_t *const *lists, con
     const int threads = small ? WinCfg<P_SMALL>::THREADS : WinCfg<P_LARGE>::THREADS;
     const size_t smem = small ? WinCfg<P_SMALL>::SMEM : WinCfg<P_LARGE>::SMEM;
     BFC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const unsigned grid = std::min<unsigned>((unsigned)(sms * per_sm), w.list_n);
-    kern<<<grid, threads, smem, s>>>(w);
+    kern<<<cap((unsigned)(sms * per_sm), c), threads, smem, s>>>(w);
     BFC_LAUNCHED();
   }
   if (any_win) profile_end(tag_of(1, MODE), s);
-  if (counts[CLS_BIG]) {
+  if (have(CLS_BIG) && big_cap > 0) {
     WArgs c = a;
-    c.list = lists[CLS_BIG];
-    c.list_n = counts[CLS_BIG];
-    c.queue = queues + CLS_BIG;
+    setup(c, CLS_BIG);
     const size_t smem = (size_t)BIG_Z * 4;
     BFC_CUDA_TRY(cudaFuncSetAttribute(k_cta_big<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const unsigned grid = std::min<unsigned>((unsigned)sms, c.list_n);
-    c.seg_cap = std::max<uint32_t>(big_cap, 1);
+    const unsigned grid = cap((unsigned)sms, CLS_BIG);
+    c.seg_cap = big_cap;
     const uint64_t need = (uint64_t)grid * c.seg_cap * 6 * 4;
     BFC_TRY(g->scr.reserve(need, s));
     c.seg = static_cast<uint32_t *>(g->scr.base());
@@ -879,7 +903,7 @@ static int launch_classes(bfc_graph *g, Plan &p, WArgs a, cudaStream_t s) {
   const uint32_t *cls = ptr<uint32_t>(p.cls);
   const uint32_t *lists[Plan::NCLS];
   for (int c = 0; c < Plan::NCLS; c++) lists[c] = cls + p.cls_begin[c];
-  return launch_lists<MODE>(g, a, lists, p.cls_count, p.big_seg_cap, s);
+  return launch_lists<MODE>(g, a, lists, p.cls_count, std::max<uint32_t>(p.big_seg_cap, 1), s);
 }
 
 static WArgs args_of(bfc_graph *g, Plan &p) {
@@ -980,7 +1004,7 @@ static int full_rows_batch(bfc_graph *g, Plan &p, int mode, const uint32_t *item
   const uint32_t *L[N];
   uint32_t C[N];
   for (int c = 0; c < N; c++) { L[c] = ptr<uint32_t>(lists) + hb[c]; C[c] = (c == 0) ? 0 : hc[c]; }
-  const uint32_t cap = (uint32_t)std::min<unsigned long long>(hmax, 0xFFFFFFFFull);
+  const uint32_t cap = std::max<uint32_t>(1, (uint32_t)std::min<unsigned long long>(hmax, 0xFFFFFFFFull));
   if (mode == MODE_LOCAL) VB_TRY(launch_lists<MODE_LOCAL>(g, a, L, C, cap, s));
   else VB_TRY(launch_lists<MODE_SINGLE>(g, a, L, C, cap, s));
   cleanup();
@@ -1037,6 +1061,44 @@ __global__ void k_finish_vertices(const uint32_t *vert_of, uint32_t nS, const un
                                   unsigned long long *bS) {
   for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nS; r += (uint64_t)gridDim.x * blockDim.x)
     bS[vert_of[r]] += bSr[r];
+}
+
+// ---------------------------------------------------------------------------
+// classification and counting without host round trips (recordable into a
+// CUDA graph): dev = 48 words: counts[16], begin[16], cursor[16]
+// ---------------------------------------------------------------------------
+__global__ void k_cls_offsets(unsigned int *dev) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    unsigned int run = 0;
+    for (int c = 0; c < Plan::NCLS; c++) {
+      dev[16 + c] = run;
+      run += dev[c];
+      dev[32 + c] = 0;
+    }
+  }
+}
+
+int plan_classify_device(Plan &p, uint32_t *cls_of, unsigned int *dev, unsigned long long *sums, cudaStream_t s) {
+  BFC_CUDA_TRY(cudaMemsetAsync(dev, 0, 48 * 4, s));
+  k_classify<<<grid_for(p.nS, 256), 256, 0, s>>>(ptr<uint64_t>(p.offR), ptr<uint64_t>(p.work), p.nS, cls_of, dev,
+                                                sums + 2 * Plan::NCLS, sums);
+  count_launch();
+  k_cls_offsets<<<1, 32, 0, s>>>(dev);
+  count_launch();
+  k_scatter_class<<<grid_for(p.nS, 256), 256, 0, s>>>(cls_of, p.nS, dev + 16, dev + 32, ptr<uint32_t>(p.cls));
+  count_launch();
+  BFC_CUDA_TRY(cudaGetLastError());
+  return BFC_OK;
+}
+
+int wedge_count_device_lists(bfc_graph *g, Plan &p, const unsigned int *dev, uint32_t big_cap,
+                             unsigned long long *d_B, cudaStream_t s) {
+  WArgs a = args_of(g, p);
+  a.B = d_B;
+  a.dev_lists = ptr<uint32_t>(p.cls);
+  a.dev_count = dev;
+  a.dev_begin = dev + 16;
+  return launch_lists<MODE_TOTAL>(g, a, nullptr, nullptr, big_cap, s);
 }
 
 int wedge_count_groups(bfc_graph *g, Plan &p, const uint32_t *grp_of_rank, unsigned long long *gB,

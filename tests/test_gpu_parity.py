@@ -172,20 +172,39 @@ def test_canonical_edges(bfc):
     assert np.array_equal(got, srt)
 
 
-def test_espar_trials_match_oracle(bfc):
+@pytest.mark.parametrize("side_stream", [False, True])
+def test_espar_trials_match_oracle(bfc, side_stream):
+    """Trial by trial; on a side stream the trials after the first replay a recorded CUDA graph."""
+    import torch
     g = synth.uniform_small(1)
+    st = torch.cuda.Stream() if side_stream else None
     with bfc.Graph(g.u, g.v, g.nU, g.nV) as G:
-        est, beta = G.espar(0.3, 6, 1234)
+        est, beta = G.espar(0.3, 6, 1234, stream=st)
     for t in range(6):
         ob, oe = O.espar_trial(g.u, g.v, g.nU, g.nV, 0.3, 1234, t)
         assert int(beta[t]) == ob
         assert est[t] == oe
 
 
-def test_clrspar_trials_match_oracle(bfc):
-    g = synth.chung_lu_scaled(3000, 9000, 40_000, 2.1, 2.4, 5)
+def test_espar_on_multi_window_graph_side_stream(bfc):
+    import torch
+    g = synth.chung_lu_scaled(120_000, 30_000, 600_000, 2.1, 2.5, 31)
+    st = torch.cuda.Stream()
     with bfc.Graph(g.u, g.v, g.nU, g.nV) as G:
-        est, beta = G.clrspar(3, 5, 99)
+        est, beta = G.espar(0.5, 3, 77, stream=st)
+        est2, beta2 = G.clrspar(2, 3, 78, stream=st)
+    for t in range(3):
+        assert int(beta[t]) == O.espar_trial(g.u, g.v, g.nU, g.nV, 0.5, 77, t)[0]
+        assert int(beta2[t]) == O.clrspar_trial(g.u, g.v, g.nU, g.nV, 2, 78, t)[0]
+
+
+@pytest.mark.parametrize("side_stream", [False, True])
+def test_clrspar_trials_match_oracle(bfc, side_stream):
+    import torch
+    g = synth.chung_lu_scaled(3000, 9000, 40_000, 2.1, 2.4, 5)
+    st = torch.cuda.Stream() if side_stream else None
+    with bfc.Graph(g.u, g.v, g.nU, g.nV) as G:
+        est, beta = G.clrspar(3, 5, 99, stream=st)
     for t in range(5):
         ob, oe = O.clrspar_trial(g.u, g.v, g.nU, g.nV, 3, 99, t)
         assert int(beta[t]) == ob
