@@ -65,6 +65,11 @@ extern "C" {
  * skew. */
 #define BFC_WHOLE_ROWS    0x100u
 
+/* bfc_exact: count the pairs among the BFC_HUB_DEFAULT highest-ranked start
+ * vertices with the tensor-core hub block (see bfc_exact_hub).  Same B. */
+#define BFC_HUB_MMA       0x200u
+#define BFC_HUB_DEFAULT   16384u
+
 typedef struct bfc_graph bfc_graph;
 typedef struct bfc_proposal bfc_proposal;
 
@@ -108,6 +113,32 @@ int bfc_graph_edges(const bfc_graph *g, uint32_t *u_out, uint32_t *v_out, void *
  * Algorithm 1's coloured line), so no halving is needed.
  * Errors: BFC_EINVAL, BFC_ECUDA, BFC_ETIMEOUT, BFC_EOVERFLOW. */
 int bfc_exact(bfc_graph *g, uint32_t flags, uint64_t *out_B, int *out_side, void *stream);
+
+/* ExactBFC with the hub-by-hub block on the tensor cores (Lemma 1 Eq. (2)-(3):
+ * c(v, w) = |Gamma_v ^ Gamma_w| is entry (v, w) of A A^T, A the 0/1 matrix of
+ * start rows against midpoint columns).  The `hubs` highest-ranked start
+ * vertices (rank: degree ascending, ties by id) form the hub set H; every
+ * pair whose lower-ranked end is in H has both ends in H, and those pairs are
+ * counted as follows:
+ *   - midpoint columns with >= tau hubs form a dense bf16 0/1 matrix A_H
+ *     (|H| x K) and the upper-triangle 128 x 128 tiles of A_H A_H^T run on
+ *     tcgen05.mma with fp32 accumulation in tensor memory (exact: every
+ *     entry is an integer <= K <= 65,536 < 2^24);
+ *   - the other columns add their hub pairs into an int32 |H| x |H| matrix;
+ *   - the tile epilogue sums C(c, 2) over v < w.
+ * The other start vertices run Algorithm 1's walk as in bfc_exact.
+ *   hubs : a multiple of 128, <= the start side's vertex count; 0 selects
+ *          min(BFC_HUB_DEFAULT, start-side count rounded down to 128)
+ *          (0 hubs when that is 0: plain bfc_exact).
+ *   tau  : dense-column threshold (>= 2); 0 picks it by a cost model (with
+ *          K <= 65,536).  An explicit tau may give K > 65,536, which stays
+ *          exact while K < 2^24 and costs |H| x K x 2 bytes.
+ *   out_stats (host, may be NULL, 4 entries): |H|, K, tau, light pairs.
+ * Device memory for the call: |H|^2 x 4 + |H| x K x 2 bytes plus 8 bytes per
+ * midpoint vertex (1.1 GB at |H| = 16,384, K = 2,048).
+ * Errors: as bfc_exact; BFC_EINVAL for a bad hubs or tau = 1. */
+int bfc_exact_hub(bfc_graph *g, uint32_t flags, uint32_t hubs, uint32_t tau, uint64_t *out_B, int *out_side,
+                  uint64_t *out_stats, void *stream);
 
 /* vBFC for every vertex (Algorithm 2; Lemma 1 Eq. (2)).
  *   bU : device, nU entries, b_u for u in U
@@ -216,7 +247,8 @@ int bfc_plan_stats(bfc_graph *g, int side, uint64_t *out, void *stream);
  * bfc_profile_read synchronises on the recorded events and returns, for the
  * kernel tag (e.g. "win.total", "warp.vertex", "big.edge"), the number of
  * launches and their summed device time in milliseconds.  Tags:
- * {warp,win,big}.{total,vertex,edge,single,local}. */
+ * {warp,win,big}.{total,vertex,edge,single,local} and hub.total (the
+ * tensor-core tile kernel of bfc_exact_hub). */
 int bfc_profile_enable(int on);
 int bfc_profile_reset(void);
 int bfc_profile_read(const char *tag, uint64_t *launches, double *total_ms);

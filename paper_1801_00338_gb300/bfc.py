@@ -28,6 +28,8 @@ BFC_SIDE_AUTO = 0x0
 BFC_SIDE_U = 0x10
 BFC_SIDE_V = 0x20
 BFC_WHOLE_ROWS = 0x100
+BFC_HUB_MMA = 0x200
+BFC_HUB_DEFAULT = 16384
 
 _lib = None
 
@@ -53,6 +55,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "bfc_graph_stats": [P, P, P, P, P, P],
         "bfc_graph_edges": [P, P, P, P],
         "bfc_exact": [P, u32, P, P, P],
+        "bfc_exact_hub": [P, u32, u32, u32, P, P, P, P],
         "bfc_per_vertex": [P, u32, P, P, P, P],
         "bfc_per_edge": [P, u32, P, P, P],
         "bfc_local_counts": [P, u32, P, P, P, P, P],
@@ -152,6 +155,7 @@ def bfc_profile_read(tag: str) -> tuple[int, float]:
 
 
 PROFILE_TAGS = [f"{c}.{m}" for c in ("warp", "win", "big") for m in ("total", "vertex", "edge", "single", "local")]
+PROFILE_TAGS.append("hub.total")
 # kernel tag -> the classes it runs
 TAG_CLASSES = {"warp": ("warp",), "win": ("s2", "s4", "s8", "s16", "s32", "l2", "l4", "l8", "l16", "l32"),
                "big": ("big",)}
@@ -209,6 +213,16 @@ def bfc_exact(h: int, flags: int = 0, stream=None) -> tuple[int, int]:
     side = ctypes.c_int()
     _check(load().bfc_exact(h, flags, ctypes.byref(B), ctypes.byref(side), _stream_ptr(stream)), "bfc_exact")
     return int(B.value), int(side.value)
+
+
+def bfc_exact_hub(h: int, flags: int = 0, hubs: int = 0, tau: int = 0, stream=None) -> tuple[int, int, dict]:
+    """ExactBFC with the tensor-core hub block; returns (B, start side, stats)."""
+    B = ctypes.c_uint64()
+    side = ctypes.c_int()
+    st = (ctypes.c_uint64 * 4)()
+    _check(load().bfc_exact_hub(h, flags, hubs, tau, ctypes.byref(B), ctypes.byref(side), st, _stream_ptr(stream)),
+           "bfc_exact_hub")
+    return int(B.value), int(side.value), dict(zip(("hubs", "K", "tau", "light_pairs"), (int(x) for x in st)))
 
 
 def bfc_per_vertex(h: int, nU: int, nV: int, flags: int = 0, stream=None):
@@ -389,8 +403,11 @@ class Graph:
         self.stats = bfc_graph_stats(self.h)
         self.m = self.stats["m"]
 
-    def exact(self, side=None, stream=None):
-        return bfc_exact(self.h, _SIDE[side], stream)
+    def exact(self, side=None, hub_mma=False, stream=None):
+        return bfc_exact(self.h, _SIDE[side] | (BFC_HUB_MMA if hub_mma else 0), stream)
+
+    def exact_hub(self, side=None, hubs=0, tau=0, stream=None):
+        return bfc_exact_hub(self.h, _SIDE[side], hubs, tau, stream)
 
     def per_vertex(self, side=None, whole_rows=False, stream=None):
         return bfc_per_vertex(self.h, self.nU, self.nV, _SIDE[side] | (BFC_WHOLE_ROWS if whole_rows else 0), stream)

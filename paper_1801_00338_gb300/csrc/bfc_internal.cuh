@@ -176,6 +176,14 @@ int plan_classify_device(Plan &p, uint32_t *cls_of, unsigned int *dev, unsigned 
 int wedge_count_device_lists(bfc_graph *g, Plan &p, const unsigned int *dev, uint32_t big_cap,
                              unsigned long long *d_B, cudaStream_t s);
 void plan_free(Plan &p, cudaStream_t s);
+// TOTAL mode over start ranks < rank_end only (ranks >= rank_end walk nothing).
+int wedge_count_below(bfc_graph *g, Plan &p, uint32_t rank_end, unsigned long long *d_B, cudaStream_t s);
+
+// hub.cu: the pairs among the top h start ranks on the tensor cores (h a
+// multiple of 128; tau = 0 picks the dense-column threshold; stats: h, K,
+// tau, light pairs, may be null).
+int hub_block_count(bfc_graph *g, Plan &p, uint32_t h, uint32_t tau, unsigned long long *d_B, uint64_t *stats,
+                    cudaStream_t s);
 // Algorithm 2 for a batch of start ranks of plan p: out[i] = b of the vertex
 // at rank item_rank[i] (every other start vertex w != v, full midpoint rows).
 int vbfc_batch(bfc_graph *g, Plan &p, const uint32_t *item_rank, uint32_t n_items, unsigned long long *out,

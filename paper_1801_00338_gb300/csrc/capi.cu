@@ -109,8 +109,29 @@ int bfc_graph_edges(const bfc_graph *g, uint32_t *u_out, uint32_t *v_out, void *
   return BFC_OK;
 }
 
+int bfc_exact_hub(bfc_graph *g, uint32_t flags, uint32_t hubs, uint32_t tau, uint64_t *out_B, int *out_side,
+                  uint64_t *out_stats, void *stream) {
+  if (!out_B || tau == 1) return BFC_EINVAL;
+  cudaStream_t s = as_stream(stream);
+  int side = 0;
+  BFC_TRY(prepare(g, flags & ~BFC_HUB_MMA, s, &side));
+  Plan &p = g->plan[side];
+  const uint32_t h = hubs ? hubs : std::min<uint32_t>(BFC_HUB_DEFAULT, p.nS / 128 * 128);
+  if (h % 128 || h > p.nS) return BFC_EINVAL;
+  if (h) {
+    BFC_TRY(hub_block_count(g, p, h, tau, acc_B(g), out_stats, s));
+  } else if (out_stats) {
+    for (int i = 0; i < 4; i++) out_stats[i] = 0;
+  }
+  BFC_TRY(wedge_count_below(g, p, p.nS - h, acc_B(g), s));
+  BFC_TRY(finish_count(g, out_B, s));
+  if (out_side) *out_side = side;
+  return BFC_OK;
+}
+
 int bfc_exact(bfc_graph *g, uint32_t flags, uint64_t *out_B, int *out_side, void *stream) {
   if (!out_B) return BFC_EINVAL;
+  if (flags & BFC_HUB_MMA) return bfc_exact_hub(g, flags, 0, 0, out_B, out_side, nullptr, stream);
   cudaStream_t s = as_stream(stream);
   int side = 0;
   BFC_TRY(prepare(g, flags, s, &side));

@@ -1,0 +1,359 @@
+// Hub-by-hub block of ExactBFC on the tensor cores (tcgen05).
+//
+// For start vertices v, w the multiplicity c(v, w) = |Gamma_v ^ Gamma_w| is
+// the (v, w) entry of A A^T, A the 0/1 adjacency matrix of start rows against
+// midpoint columns (Lemma 1, Eq. (2)-(3)).  Among the h highest-ranked start
+// vertices ("hubs") this product is dense enough for a matrix engine:
+//   - heavy columns (midpoints with >= tau hub neighbours) form a dense bf16
+//     0/1 matrix A_H (h x K); the upper-triangle 128 x 128 tiles of
+//     A_H A_H^T are computed by tcgen05.mma (kind::f16, fp32 accumulation in
+//     tensor memory, exact because every entry is an integer below 2^24);
+//   - light columns (2 <= hub neighbours < tau) add their hub pairs into an
+//     int32 matrix C_L with atomics;
+//   - the epilogue reads each accumulator tile, adds C_L and sums C(c, 2) over
+//     the pairs i < j.
+// A hub's later vertices (rank order) are all hubs, so the block counts every
+// pair whose first vertex is a hub; the window kernels skip hub start vertices
+// and count all other pairs as before.
+#include <algorithm>
+#include <vector>
+
+#include "bfc_internal.cuh"
+
+namespace bfc {
+namespace {
+
+constexpr int TM = 128;          // tile rows / columns
+constexpr int KC = 64;           // K elements per staged chunk (4 MMAs of K = 16)
+constexpr int HB_THREADS = 128;  // one warpgroup
+constexpr int HB_PER_SM = 4;     // 4 x 128 TMEM columns = 512
+constexpr uint64_t WAIT_NS = 1000000000ull;  // bounded waits give up after ~1 s
+constexpr size_t HB_SMEM = 52 * 1024;     // 32 KB of operands, sized so at most 4 CTAs share an SM
+                                          // (4 x 128 TMEM columns = all 512)
+
+unsigned hb_grid(uint64_t n, unsigned threads, unsigned cap = 152 * 16) {
+  uint64_t g = (n + threads - 1) / threads;
+  if (g > cap) g = cap;
+  if (g == 0) g = 1;
+  return (unsigned)g;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// K-major operand layout without swizzle: 8-row x 16-byte core matrices; the
+// core matrix of rows 8g.. and elements 8c.. sits at g * SBO + c * LBO.
+constexpr uint32_t LBO = 128, SBO = (KC / 8) * 128;
+__device__ __forceinline__ uint32_t core_off(int row, int kgroup) {
+  return (uint32_t)((row >> 3) * SBO + kgroup * LBO + (row & 7) * 16);
+}
+
+// shared memory matrix descriptor (tcgen05): start, leading and stride byte
+// offsets in 16-byte units, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((LBO >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((SBO >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// instruction descriptor: D fp32, A and B bf16, both K-major, M = N = 128
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TM >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+
+// ---------------------------------------------------------------------------
+// column split
+// ---------------------------------------------------------------------------
+// hub degree of every midpoint: its row (ascending ranks) ends with its hubs
+__global__ void k_hub_degree(const uint64_t *offM, const uint32_t *mR, uint32_t nM, uint32_t hub0, uint32_t *hd,
+                             unsigned int *hist, uint32_t hist_n) {
+  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nM; x += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t lo = offM[x], hi = offM[x + 1];
+    const uint64_t end = hi;
+    while (lo < hi) {  // first entry with rank >= hub0
+      const uint64_t mid = (lo + hi) / 2;
+      if (mR[mid] < hub0) lo = mid + 1; else hi = mid;
+    }
+    const uint32_t d = (uint32_t)(end - lo);
+    hd[x] = d;
+    if (d >= 2) atomicAdd(&hist[d < hist_n ? d : hist_n - 1], 1u);
+  }
+}
+
+__global__ void k_heavy_list(const uint32_t *hd, uint32_t nM, uint32_t tau, unsigned int *count, uint32_t *cols) {
+  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nM; x += (uint64_t)gridDim.x * blockDim.x)
+    if (hd[x] >= tau) cols[atomicAdd(count, 1u)] = (uint32_t)x;
+}
+
+// A_H[hub][k] = 1 for the hubs of heavy column k (one warp per column; the
+// hubs are the suffix of the column's rank-sorted row)
+__global__ void k_fill_dense(const uint64_t *offM, const uint32_t *mR, const uint32_t *hd, const uint32_t *cols,
+                             uint32_t K, uint32_t Kp, uint32_t hub0, uint16_t *A) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t k = warp; k < K; k += nw) {
+    const uint32_t x = cols[k];
+    const uint64_t e = offM[x + 1], b = e - hd[x];
+    for (uint64_t i = b + lane; i < e; i += 32) A[(uint64_t)(mR[i] - hub0) * Kp + k] = 0x3F80;  // bf16 1.0
+  }
+}
+
+// light columns: every hub pair (a < b) of the column adds one to C_L[a][b]
+// (one warp per column: the first hub in turn, lanes over the second)
+__global__ void k_light_pairs(const uint64_t *offM, const uint32_t *mR, const uint32_t *hd, uint32_t nM,
+                              uint32_t tau, uint32_t hub0, uint32_t h, unsigned int *CL,
+                              unsigned long long *npairs) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long mine = 0;
+  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t x = warp; x < nM; x += nw) {
+    const uint32_t d = hd[x];
+    if (d < 2 || d >= tau) continue;
+    const uint64_t e = offM[x + 1], b = e - d;  // the d hubs, ascending ranks
+    mine += (uint64_t)d * (d - 1) / 2;
+    for (uint32_t i = 0; i + 1 < d; i++) {
+      const uint64_t row = (uint64_t)(mR[b + i] - hub0) * h - hub0;
+      for (uint32_t j = i + 1 + lane; j < d; j += 32) atomicAdd(&CL[row + mR[b + j]], 1u);
+    }
+  }
+  if (lane == 0 && mine) atomicAdd(npairs, mine);
+}
+
+// ---------------------------------------------------------------------------
+// tensor-core tiles: C_ij = A_i A_j^T over upper-triangle tile pairs (ti <= tj)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void tile_of(uint32_t t, uint32_t nt, uint32_t &ti, uint32_t &tj) {
+  // enumerate (ti, tj), ti <= tj, row by row
+  uint32_t i = 0, rem = t;
+  while (rem >= nt - i) { rem -= nt - i; i++; }
+  ti = i;
+  tj = i + rem;
+}
+
+// Wait for phase `parity` of an mbarrier for at most about one second of
+// global time; returns 1 when the phase completed.
+__device__ __forceinline__ uint32_t mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  uint64_t t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity));
+    if (done) return 1;
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > WAIT_NS) return 0;
+  }
+}
+
+// One CTA (one warpgroup) per tile at a time, tiles from a global queue.
+// Per 64-wide K chunk: the CTA stages A_i and A_j rows into the canonical
+// K-major layout, one thread issues four 128x128x16 MMAs into the CTA's 128
+// TMEM columns and commits them to an mbarrier, and all threads wait for it
+// before the chunk's buffers are refilled.  The epilogue reads the 128 x 128
+// fp32 accumulator (TMEM lane = tile row), adds C_L and sums C(c, 2).
+__global__ void __launch_bounds__(HB_THREADS) k_hub_mma(const uint16_t *A, uint32_t Kp, uint32_t h,
+                                                        const unsigned int *CL, unsigned int *queue,
+                                                        unsigned long long *B, uint32_t *err) {
+  extern __shared__ __align__(1024) uint8_t hub_smem[];
+  uint8_t *sa = hub_smem, *sb = hub_smem + TM * KC * 2;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_holder, sh_tile;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
+                 "r"(TM));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t taddr = tmem_holder;
+  const uint32_t nt = h / TM, ntiles = nt * (nt + 1) / 2, nchunks = Kp / KC;
+  uint32_t phase = 0;
+  bool ok = true;
+  unsigned long long acc = 0;
+  while (ok) {
+    if (tid == 0) sh_tile = atomicAdd(queue, 1u);
+    __syncthreads();
+    const uint32_t t = sh_tile;
+    if (t >= ntiles) break;
+    uint32_t ti, tj;
+    tile_of(t, nt, ti, tj);
+    const uint16_t *Ai = A + (uint64_t)ti * TM * Kp, *Aj = A + (uint64_t)tj * TM * Kp;
+    for (uint32_t kc = 0; kc < nchunks; kc++) {
+      // stage: 8 threads per row, 16 bytes each (128-byte row pieces)
+      for (int q = tid; q < TM * (KC / 8); q += HB_THREADS) {
+        const int row = q >> 3, g = q & 7;
+        const uint64_t goff = (uint64_t)row * Kp + (uint64_t)kc * KC + g * 8;
+        *reinterpret_cast<uint4 *>(sa + core_off(row, g)) = __ldg(reinterpret_cast<const uint4 *>(Ai + goff));
+        *reinterpret_cast<uint4 *>(sb + core_off(row, g)) = __ldg(reinterpret_cast<const uint4 *>(Aj + goff));
+      }
+      asm volatile("fence.proxy.async.shared::cta;");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      if (tid == 0) {
+#pragma unroll
+        for (int k = 0; k < KC / 16; k++) {
+          const uint64_t ad = smem_desc(smem_u32(sa) + k * 2 * LBO);
+          const uint64_t bd = smem_desc(smem_u32(sb) + k * 2 * LBO);
+          const uint32_t accum = (kc > 0 || k > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr),
+              "l"(ad), "l"(bd), "r"(IDESC), "r"(accum));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&mbar)));
+      }
+      const uint32_t done = mbar_wait_bounded(smem_u32(&mbar), phase);
+      phase ^= 1;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      ok = __syncthreads_and(done) != 0;  // uniform across the CTA
+      if (!ok) break;
+    }
+    if (!ok) {
+      if (tid == 0) atomicOr(err, DERR_TIMEOUT);
+      break;
+    }
+    // epilogue: row i of the tile is TMEM lane i; sum C(c, 2) over global i < j
+    const uint32_t gi = ti * TM + 32 * warp + lane;
+    for (int c0 = 0; c0 < TM; c0 += 8) {
+      uint32_t r[8];
+      const uint32_t ta = taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                   : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                   : "r"(ta));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        const uint32_t gj = tj * TM + c0 + q;
+        if (gj <= gi) continue;
+        const uint64_t c = (uint64_t)__uint_as_float(r[q]) + CL[(uint64_t)gi * h + gj];
+        if (c > 1) acc += c * (c - 1) / 2;
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+  }
+  if (!ok) {
+    // a commit that never arrived: give the MMAs in flight one more bounded
+    // wait before the columns are released
+    mbar_wait_bounded(smem_u32(&mbar), phase ^ 1);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0 && acc) atomicAdd(B, acc);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TM));
+}
+
+int sm_count_hub() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 152;
+}
+
+}  // namespace
+
+// Count every pair of start vertices whose lower-ranked vertex is one of the
+// top h ranks (both are then hubs), adding sum C(c, 2) to d_B.  h: a multiple
+// of 128, <= nS.  tau: columns with >= tau hubs go to the dense product (0:
+// chosen by a cost model).  stats (host, may be null, 4 entries): h, K (dense
+// columns), tau, light pairs.
+int hub_block_count(bfc_graph *g, Plan &p, uint32_t h, uint32_t tau, unsigned long long *d_B, uint64_t *stats,
+                    cudaStream_t s) {
+  if (h == 0 || h % TM || h > p.nS || tau == 1) return BFC_EINVAL;
+  const uint32_t hub0 = p.nS - h, nM = p.nM;
+  constexpr uint32_t HIST = 4096;
+  DBuf hd, hist, cnt, cols, A, CL;
+  auto cleanup = [&]() { DBuf *bs[] = {&hd, &hist, &cnt, &cols, &A, &CL}; for (DBuf *b : bs) dfree(*b, s); };
+  int rc = BFC_OK;
+#define HB_TRY(x) do { rc = (x); if (rc) { cleanup(); return rc; } } while (0)
+#define HB_CUDA(x) do { if ((x) != cudaSuccess) { cleanup(); return BFC_ECUDA; } } while (0)
+  HB_TRY(dalloc(hd, (uint64_t)std::max<uint32_t>(nM, 1) * 4, s));
+  HB_TRY(dalloc(cols, (uint64_t)std::max<uint32_t>(nM, 1) * 4, s));
+  HB_TRY(dalloc(hist, HIST * 4, s));
+  HB_TRY(dalloc(cnt, 32, s));
+  HB_CUDA(cudaMemsetAsync(hist.p, 0, HIST * 4, s));
+  HB_CUDA(cudaMemsetAsync(cnt.p, 0, 32, s));
+  unsigned int *heavy_n = ptr<unsigned int>(cnt), *queue = heavy_n + 1;
+  unsigned long long *light_n = reinterpret_cast<unsigned long long *>(ptr<unsigned int>(cnt) + 2);
+  if (nM) {
+    k_hub_degree<<<hb_grid(nM, 256), 256, 0, s>>>(p.offM, ptr<uint32_t>(p.mR), nM, hub0, ptr<uint32_t>(hd),
+                                                  ptr<unsigned int>(hist), HIST);
+    count_launch();
+  }
+  if (tau == 0) {
+    // cost model: a dense column costs every tile 2 x 128 x 2 bytes of operand
+    // staging (L2-resident A_H) plus its MMA work; a light column costs
+    // C(d, 2) scattered atomics.  Columns lumped in the last bin stay dense.
+    std::vector<unsigned int> hh(HIST);
+    HB_CUDA(cudaMemcpyAsync(hh.data(), hist.p, HIST * 4, cudaMemcpyDeviceToHost, s));
+    HB_CUDA(cudaStreamSynchronize(s));
+    const double tiles = (double)(h / TM) * (h / TM + 1) / 2;
+    const double per_col = tiles * (512.0 / 4.0e12 + 2.0 * TM * TM / 1.5e15);
+    const double per_pair = 1.0 / 1.5e11;
+    std::vector<double> cols_ge(HIST + 1, 0.0), pairs_lt(HIST + 1, 0.0);
+    for (int d = HIST - 1; d >= 0; d--) cols_ge[d] = cols_ge[d + 1] + hh[d];
+    for (uint32_t d = 1; d <= HIST; d++) pairs_lt[d] = pairs_lt[d - 1] + (double)hh[d - 1] * (d - 1) * (d - 2) / 2.0;
+    double best = 1e300;
+    tau = HIST - 1;
+    for (uint32_t t = 2; t < HIST; t++) {
+      if (cols_ge[t] > 65536.0) continue;  // A_H stays within h x 65,536 x 2 bytes
+      const double cost = cols_ge[t] * per_col + pairs_lt[t] * per_pair;
+      if (cost < best) { best = cost; tau = t; }
+    }
+  }
+  if (nM) {
+    k_heavy_list<<<hb_grid(nM, 256), 256, 0, s>>>(ptr<uint32_t>(hd), nM, tau, heavy_n, ptr<uint32_t>(cols));
+    count_launch();
+  }
+  unsigned int K = 0;
+  HB_CUDA(cudaMemcpyAsync(&K, heavy_n, 4, cudaMemcpyDeviceToHost, s));
+  HB_CUDA(cudaStreamSynchronize(s));
+  const uint32_t Kp = std::max<uint32_t>(KC, (K + KC - 1) / KC * KC);
+  HB_TRY(dalloc(A, (uint64_t)h * Kp * 2, s));
+  HB_TRY(dalloc(CL, (uint64_t)h * h * 4, s));
+  HB_CUDA(cudaMemsetAsync(A.p, 0, (uint64_t)h * Kp * 2, s));
+  HB_CUDA(cudaMemsetAsync(CL.p, 0, (uint64_t)h * h * 4, s));
+  if (K) {
+    k_fill_dense<<<hb_grid((uint64_t)K * 32, 256), 256, 0, s>>>(p.offM, ptr<uint32_t>(p.mR), ptr<uint32_t>(hd),
+                                                                ptr<uint32_t>(cols), K, Kp, hub0, ptr<uint16_t>(A));
+    count_launch();
+  }
+  if (nM) {
+    k_light_pairs<<<hb_grid((uint64_t)nM * 32, 256), 256, 0, s>>>(p.offM, ptr<uint32_t>(p.mR), ptr<uint32_t>(hd),
+                                                                  nM, tau, hub0, h, ptr<unsigned int>(CL), light_n);
+    count_launch();
+  }
+  const uint64_t ntiles = (uint64_t)(h / TM) * (h / TM + 1) / 2;
+  const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)sm_count_hub() * HB_PER_SM, ntiles);
+  HB_CUDA(cudaFuncSetAttribute(k_hub_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HB_SMEM));
+  profile_begin("hub.total", s);
+  k_hub_mma<<<grid, HB_THREADS, HB_SMEM, s>>>(ptr<uint16_t>(A), Kp, h, ptr<unsigned int>(CL), queue, d_B,
+                                              ptr<uint32_t>(g->err));
+  count_launch();
+  profile_end("hub.total", s);
+  HB_CUDA(cudaGetLastError());
+  unsigned long long lp = 0;
+  HB_CUDA(cudaMemcpyAsync(&lp, light_n, 8, cudaMemcpyDeviceToHost, s));
+  HB_CUDA(cudaStreamSynchronize(s));  // the temporaries are freed below
+  if (stats) {
+    stats[0] = h;
+    stats[1] = K;
+    stats[2] = tau;
+    stats[3] = lp;
+  }
+  cleanup();
+#undef HB_TRY
+#undef HB_CUDA
+  return BFC_OK;
+}
+
+}  // namespace bfc

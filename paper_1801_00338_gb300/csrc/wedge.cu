@@ -109,6 +109,9 @@ struct WArgs {
   const uint32_t *dev_lists;
   const unsigned int *dev_begin, *dev_count;
   uint32_t cls;
+  // start ranks >= rank_end walk nothing (their pairs are counted by the
+  // hub block); nS otherwise
+  uint32_t rank_end;
 };
 
 // resolve the vertex list of a launch (host-known or device-resident)
@@ -221,7 +224,7 @@ __global__ void __launch_bounds__(WH_WARPS * 32) k_warp_class(WArgs a) {
     if (idx >= a.list_n) break;
     const uint32_t item = a.list[idx];
     const uint32_t r = (MODE == MODE_SINGLE) ? a.item_rank[item] : item;
-    const uint64_t rb = a.offR[r], re = a.offR[r + 1];
+    const uint64_t rb = a.offR[r], re = (r < a.rank_end) ? a.offR[r + 1] : rb;  // ranks >= rank_end: done elsewhere
     warp_for_each_wedge<Full<MODE>::value>(a, rb, re, [&](uint32_t i, uint64_t) {
       const uint32_t w = a.mR[i];
       if (!Full<MODE>::value || w != r) wh_insert(keys, cnts, w);
@@ -391,7 +394,7 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, P) k_cta_win(WArgs a) {
     if (idx >= a.list_n) break;
     const uint32_t item = a.list[idx];
     const uint32_t r = (MODE == MODE_SINGLE) ? a.item_rank[item] : item;
-    const uint64_t rb = a.offR[r], re = a.offR[r + 1];
+    const uint64_t rb = a.offR[r], re = (r < a.rank_end) ? a.offR[r + 1] : rb;  // ranks >= rank_end: done elsewhere
     // ---- segments of the vertex's wedge lists
     for (uint64_t base = rb; base < re; base += WIN_THREADS) {
       const uint64_t j = base + threadIdx.x;
@@ -566,7 +569,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_big(WArgs a) {
     if (idx >= a.list_n) break;
     const uint32_t item = a.list[idx];
     const uint32_t r = (MODE == MODE_SINGLE) ? a.item_rank[item] : item;
-    const uint64_t rb = a.offR[r], re = a.offR[r + 1];
+    const uint64_t rb = a.offR[r], re = (r < a.rank_end) ? a.offR[r + 1] : rb;  // ranks >= rank_end: done elsewhere
     for (uint64_t base = rb; base < re; base += CT_THREADS) {
       uint64_t j = base + threadIdx.x;
       uint32_t b = 0, e = 0, ns = 0;
@@ -909,6 +912,7 @@ static int launch_classes(bfc_graph *g, Plan &p, WArgs a, cudaStream_t s) {
 static WArgs args_of(bfc_graph *g, Plan &p) {
   WArgs a{};
   a.nS = p.nS;
+  a.rank_end = p.nS;
   a.offR = ptr<uint64_t>(p.offR);
   a.sX = ptr<uint32_t>(p.sX);
   a.sEid = ptr<uint32_t>(p.sEid);
@@ -1107,6 +1111,13 @@ int wedge_count_groups(bfc_graph *g, Plan &p, const uint32_t *grp_of_rank, unsig
   a.B = d_B;
   a.grp = grp_of_rank;
   a.gB = gB;
+  return launch_classes<MODE_TOTAL>(g, p, a, s);
+}
+
+int wedge_count_below(bfc_graph *g, Plan &p, uint32_t rank_end, unsigned long long *d_B, cudaStream_t s) {
+  WArgs a = args_of(g, p);
+  a.B = d_B;
+  a.rank_end = rank_end;
   return launch_classes<MODE_TOTAL>(g, p, a, s);
 }
 

@@ -75,3 +75,15 @@ def test_start_side_invariance(big):
     B, _ = G.exact()
     assert G.exact("U")[0] == B
     assert G.exact("V")[0] == B  # 35x the wedges (centred on U), same count
+
+
+def test_hub_block_same_count(big):
+    """The tensor-core hub block (top 16,384 U ranks) in the benchmark's
+    configuration gives the walk's count."""
+    g, G = big
+    B, _ = G.exact()
+    Bh, side, st = G.exact_hub()
+    assert side == 0 and st["hubs"] == 16384
+    assert 0 < st["K"] <= 65536 and st["light_pairs"] > 0
+    assert Bh == B
+    assert G.exact(hub_mma=True)[0] == B
