@@ -37,13 +37,16 @@ CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.a
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
 
-def measured_peaks():
+def measured_peaks(key: str = "hbm_gbs"):
+    """(peak, 'measured' | 'fallback') for hbm_gbs (GB/s) or a bf16 TFLOP/s key."""
+    fallback = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
-    return 6800.0, "fallback"
+        if key in d:
+            return float(d[key]), "measured"
+    return fallback[key], "fallback"
 
 
 class ClockSampler:
@@ -200,7 +203,7 @@ def run_own(args, rank, world, local_rank):
     def step():
         h = bfc.bfc_graph_from_edges(du, dv, nU, nV, 0, sptr)
         try:
-            bfc._check(L.bfc_exact(h, 0, ctypes.byref(Bh), ctypes.byref(side_h), sptr), "bfc_exact")
+            bfc._check(L.bfc_exact(h, bfc.BFC_HUB_MMA, ctypes.byref(Bh), ctypes.byref(side_h), sptr), "bfc_exact")
             bfc._check(L.bfc_local_counts(h, 0, bU.data_ptr(), bV.data_ptr(), be.data_ptr(), ctypes.byref(B2h), sptr),
                        "bfc_local_counts")
         finally:
@@ -211,6 +214,8 @@ def run_own(args, rank, world, local_rank):
     # statistics of the workload (not timed)
     G = bfc.Graph(du, dv, nU, nV)
     Bval, side = G.exact()
+    Bhub, _, hub_stats = G.exact_hub()
+    assert Bhub == Bval
     st = G.stats
     W = st["wedges_v"] if side == 0 else st["wedges_u"]
     ps = G.plan_stats(side)
@@ -258,7 +263,7 @@ def run_own(args, rank, world, local_rank):
                    "bfc_graph_from_edges")
         h = hh.value
         try:
-            bfc._check(L.bfc_exact(h, 0, ctypes.byref(Bh), ctypes.byref(side_h), sptr), "bfc_exact")
+            bfc._check(L.bfc_exact(h, bfc.BFC_HUB_MMA, ctypes.byref(Bh), ctypes.byref(side_h), sptr), "bfc_exact")
             bfc._check(L.bfc_local_counts(h, 0, bU.data_ptr(), bV.data_ptr(), be.data_ptr(), ctypes.byref(B2h), sptr),
                        "bfc_local_counts")
             obU.copy_(bU, non_blocking=True)
@@ -284,7 +289,7 @@ def run_own(args, rank, world, local_rank):
 
     # ---- roofline of the dominant kernel
     peak, peak_kind = measured_peaks()
-    dom = max(prof, key=lambda t: prof[t][1])
+    dom = max((t for t in prof if t.split(".")[0] in bfc.TAG_CLASSES), key=lambda t: prof[t][1])
     n_launch, tot_ms = prof[dom]
     cls = dom.split(".")[0]
     mode = dom.split(".")[1]
@@ -301,6 +306,20 @@ def run_own(args, rank, world, local_rank):
                 "traffic": None, "kernel": {"warp": "k_warp_class", "win": "k_cta_win", "big": "k_cta_big"}[cls] + f"<{mode}>", "peak_kind": peak_kind,
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms}
 
+    # the hub block's tile kernel: upper-triangle 128 x 128 tiles over K padded to 64
+    nt = hub_stats["hubs"] // 128
+    Kp = max(64, -(-hub_stats["K"] // 64) * 64)
+    hub_flops = nt * (nt + 1) // 2 * 128 * 128 * Kp * 2
+    hn, hms = prof.get("hub.total", (0, 0.0))
+    hub_roof = None
+    if hn and hms > 0:
+        tpk, tkind = measured_peaks("bf16_tflops_sustained")  # timed inside the long step
+        ach = hub_flops / (hms / hn / 1e3) / 1e12
+        hub_roof = {"bound": "tensor", "kernel": "k_hub_mma", "achieved": ach, "peak": tpk, "unit": "TFLOP/s",
+                    "frac": ach / tpk, "peak_kind": tkind, "flops_per_launch": hub_flops, "avg_launch_ms": hms / hn,
+                    "hubs": hub_stats["hubs"], "K": hub_stats["K"], "tau": hub_stats["tau"],
+                    "light_pairs": hub_stats["light_pairs"]}
+
     line = {
         "metric": METRIC, "value": value, "unit": "wedges/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -313,6 +332,7 @@ def run_own(args, rank, world, local_rank):
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "roofline": roofline,
+        "roofline_hub_block": hub_roof,
         "kernels_ms_per_step": {t: prof[t][1] / args.steps for t in prof if prof[t][0]},
     }
     if rank == 0 and not args.no_cpu_baseline:

@@ -65,10 +65,10 @@ extern "C" {
  * skew. */
 #define BFC_WHOLE_ROWS    0x100u
 
-/* bfc_exact: count the pairs among the BFC_HUB_DEFAULT highest-ranked start
- * vertices with the tensor-core hub block (see bfc_exact_hub).  Same B. */
+/* bfc_exact: count the pairs among the highest-ranked start vertices with the
+ * tensor-core hub block (bfc_exact_hub with its automatic hub set).  Same B. */
 #define BFC_HUB_MMA       0x200u
-#define BFC_HUB_DEFAULT   16384u
+#define BFC_HUB_MAX       16384u
 
 typedef struct bfc_graph bfc_graph;
 typedef struct bfc_proposal bfc_proposal;
@@ -128,8 +128,10 @@ int bfc_exact(bfc_graph *g, uint32_t flags, uint64_t *out_B, int *out_side, void
  *   - the tile epilogue sums C(c, 2) over v < w.
  * The other start vertices run Algorithm 1's walk as in bfc_exact.
  *   hubs : a multiple of 128, <= the start side's vertex count; 0 selects
- *          min(BFC_HUB_DEFAULT, start-side count rounded down to 128)
- *          (0 hubs when that is 0: plain bfc_exact).
+ *          it: the fewest top ranks (a multiple of 128, at most BFC_HUB_MAX)
+ *          that hold every start vertex whose wedge lists exceed the walk's
+ *          largest shared-memory window, i.e. the vertices the walk serves
+ *          from global-memory cursors; none such: no hubs (plain bfc_exact).
  *   tau  : dense-column threshold (>= 2); 0 picks it by a cost model (with
  *          K <= 65,536).  An explicit tau may give K > 65,536, which stays
  *          exact while K < 2^24 and costs |H| x K x 2 bytes.
@@ -247,8 +249,8 @@ int bfc_plan_stats(bfc_graph *g, int side, uint64_t *out, void *stream);
  * bfc_profile_read synchronises on the recorded events and returns, for the
  * kernel tag (e.g. "win.total", "warp.vertex", "big.edge"), the number of
  * launches and their summed device time in milliseconds.  Tags:
- * {warp,win,big}.{total,vertex,edge,single,local} and hub.total (the
- * tensor-core tile kernel of bfc_exact_hub). */
+ * {warp,win,big}.{total,vertex,edge,single,local}, and for bfc_exact_hub
+ * hub.total (the tensor-core tile kernel), hub.degree and hub.light. */
 int bfc_profile_enable(int on);
 int bfc_profile_reset(void);
 int bfc_profile_read(const char *tag, uint64_t *launches, double *total_ms);

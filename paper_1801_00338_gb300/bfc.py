@@ -29,7 +29,7 @@ BFC_SIDE_U = 0x10
 BFC_SIDE_V = 0x20
 BFC_WHOLE_ROWS = 0x100
 BFC_HUB_MMA = 0x200
-BFC_HUB_DEFAULT = 16384
+BFC_HUB_MAX = 16384
 
 _lib = None
 
@@ -155,7 +155,7 @@ def bfc_profile_read(tag: str) -> tuple[int, float]:
 
 
 PROFILE_TAGS = [f"{c}.{m}" for c in ("warp", "win", "big") for m in ("total", "vertex", "edge", "single", "local")]
-PROFILE_TAGS.append("hub.total")
+PROFILE_TAGS += ["hub.total", "hub.degree", "hub.light"]
 # kernel tag -> the classes it runs
 TAG_CLASSES = {"warp": ("warp",), "win": ("s2", "s4", "s8", "s16", "s32", "l2", "l4", "l8", "l16", "l32"),
                "big": ("big",)}

@@ -184,6 +184,8 @@ int wedge_count_below(bfc_graph *g, Plan &p, uint32_t rank_end, unsigned long lo
 // tau, light pairs, may be null).
 int hub_block_count(bfc_graph *g, Plan &p, uint32_t h, uint32_t tau, unsigned long long *d_B, uint64_t *stats,
                     cudaStream_t s);
+// The automatic hub count (top ranks covering the walk's big class, <= max_h).
+int hub_auto_size(Plan &p, uint32_t max_h, uint32_t *h, cudaStream_t s);
 // Algorithm 2 for a batch of start ranks of plan p: out[i] = b of the vertex
 // at rank item_rank[i] (every other start vertex w != v, full midpoint rows).
 int vbfc_batch(bfc_graph *g, Plan &p, const uint32_t *item_rank, uint32_t n_items, unsigned long long *out,

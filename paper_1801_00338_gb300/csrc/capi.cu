@@ -116,7 +116,8 @@ int bfc_exact_hub(bfc_graph *g, uint32_t flags, uint32_t hubs, uint32_t tau, uin
   int side = 0;
   BFC_TRY(prepare(g, flags & ~BFC_HUB_MMA, s, &side));
   Plan &p = g->plan[side];
-  const uint32_t h = hubs ? hubs : std::min<uint32_t>(BFC_HUB_DEFAULT, p.nS / 128 * 128);
+  uint32_t h = hubs;
+  if (h == 0) BFC_TRY(hub_auto_size(p, BFC_HUB_MAX, &h, s));
   if (h % 128 || h > p.nS) return BFC_EINVAL;
   if (h) {
     BFC_TRY(hub_block_count(g, p, h, tau, acc_B(g), out_stats, s));

@@ -60,9 +60,15 @@ constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TM >
 // ---------------------------------------------------------------------------
 // column split
 // ---------------------------------------------------------------------------
-// hub degree of every midpoint: its row (ascending ranks) ends with its hubs
+// hub degree of every midpoint: its row (ascending ranks) ends with its hubs.
+// The histogram of hub degrees >= 2 is gathered per block in shared memory
+// (most columns have small hub degrees: one global bin would serialise).
+constexpr uint32_t HIST = 4096;
 __global__ void k_hub_degree(const uint64_t *offM, const uint32_t *mR, uint32_t nM, uint32_t hub0, uint32_t *hd,
-                             unsigned int *hist, uint32_t hist_n) {
+                             unsigned int *hist) {
+  __shared__ unsigned int sh[HIST];
+  for (uint32_t i = threadIdx.x; i < HIST; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
   for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nM; x += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t lo = offM[x], hi = offM[x + 1];
     const uint64_t end = hi;
@@ -72,8 +78,11 @@ __global__ void k_hub_degree(const uint64_t *offM, const uint32_t *mR, uint32_t 
     }
     const uint32_t d = (uint32_t)(end - lo);
     hd[x] = d;
-    if (d >= 2) atomicAdd(&hist[d < hist_n ? d : hist_n - 1], 1u);
+    if (d >= 2) atomicAdd(&sh[d < HIST ? d : HIST - 1], 1u);
   }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < HIST; i += blockDim.x)
+    if (sh[i]) atomicAdd(&hist[i], sh[i]);
 }
 
 __global__ void k_heavy_list(const uint32_t *hd, uint32_t nM, uint32_t tau, unsigned int *count, uint32_t *cols) {
@@ -252,6 +261,14 @@ __global__ void __launch_bounds__(HB_THREADS) k_hub_mma(const uint16_t *A, uint3
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TM));
 }
 
+__global__ void k_min_rank(const uint32_t *list, uint32_t n, unsigned int *out) {
+  unsigned int mine = 0xFFFFFFFFu;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    mine = min(mine, list[i]);
+  for (int o = 16; o > 0; o >>= 1) mine = min(mine, __shfl_down_sync(0xffffffffu, mine, o));
+  if ((threadIdx.x & 31) == 0 && mine != 0xFFFFFFFFu) atomicMin(out, mine);
+}
+
 int sm_count_hub() {
   int dev = 0, n = 0;
   cudaGetDevice(&dev);
@@ -260,6 +277,36 @@ int sm_count_hub() {
 }
 
 }  // namespace
+
+// Automatic hub count: the smallest multiple of 128 whose top ranks hold every
+// vertex of the big class (the start vertices whose wedge lists exceed the
+// large windows' segment capacity: the walk's most expensive vertices), at
+// most max_h; 0 when the class is empty.
+int hub_auto_size(Plan &p, uint32_t max_h, uint32_t *h, cudaStream_t s) {
+  constexpr int BIG = Plan::NCLS - 1;
+  *h = 0;
+  const uint32_t n = p.cls_count[BIG];
+  if (n == 0 || p.nS < TM) return BFC_OK;
+  DBuf out;
+  BFC_TRY(dalloc(out, 4, s));
+  unsigned int lo = 0xFFFFFFFFu;
+  int rc = BFC_OK;
+  if (cudaMemcpyAsync(out.p, &lo, 4, cudaMemcpyHostToDevice, s) != cudaSuccess) rc = BFC_ECUDA;
+  if (!rc) {
+    k_min_rank<<<hb_grid(n, 256, 152), 256, 0, s>>>(ptr<uint32_t>(p.cls) + p.cls_begin[BIG], n,
+                                                     ptr<unsigned int>(out));
+    count_launch();
+    if (cudaMemcpyAsync(&lo, out.p, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      rc = BFC_ECUDA;
+  }
+  dfree(out, s);
+  if (rc) return rc;
+  const uint64_t cover = (uint64_t)p.nS - lo;
+  const uint64_t hh = std::min<uint64_t>((cover + TM - 1) / TM * TM, std::min<uint64_t>(max_h, p.nS) / TM * TM);
+  *h = (uint32_t)hh;
+  return BFC_OK;
+}
 
 // Count every pair of start vertices whose lower-ranked vertex is one of the
 // top h ranks (both are then hubs), adding sum C(c, 2) to d_B.  h: a multiple
@@ -270,7 +317,6 @@ int hub_block_count(bfc_graph *g, Plan &p, uint32_t h, uint32_t tau, unsigned lo
                     cudaStream_t s) {
   if (h == 0 || h % TM || h > p.nS || tau == 1) return BFC_EINVAL;
   const uint32_t hub0 = p.nS - h, nM = p.nM;
-  constexpr uint32_t HIST = 4096;
   DBuf hd, hist, cnt, cols, A, CL;
   auto cleanup = [&]() { DBuf *bs[] = {&hd, &hist, &cnt, &cols, &A, &CL}; for (DBuf *b : bs) dfree(*b, s); };
   int rc = BFC_OK;
@@ -285,9 +331,11 @@ int hub_block_count(bfc_graph *g, Plan &p, uint32_t h, uint32_t tau, unsigned lo
   unsigned int *heavy_n = ptr<unsigned int>(cnt), *queue = heavy_n + 1;
   unsigned long long *light_n = reinterpret_cast<unsigned long long *>(ptr<unsigned int>(cnt) + 2);
   if (nM) {
-    k_hub_degree<<<hb_grid(nM, 256), 256, 0, s>>>(p.offM, ptr<uint32_t>(p.mR), nM, hub0, ptr<uint32_t>(hd),
-                                                  ptr<unsigned int>(hist), HIST);
+    profile_begin("hub.degree", s);
+    k_hub_degree<<<hb_grid(nM, 256, 152 * 4), 256, 0, s>>>(p.offM, ptr<uint32_t>(p.mR), nM, hub0, ptr<uint32_t>(hd),
+                                                  ptr<unsigned int>(hist));
     count_launch();
+    profile_end("hub.degree", s);
   }
   if (tau == 0) {
     // cost model: a dense column costs every tile 2 x 128 x 2 bytes of operand
@@ -328,9 +376,11 @@ int hub_block_count(bfc_graph *g, Plan &p, uint32_t h, uint32_t tau, unsigned lo
     count_launch();
   }
   if (nM) {
+    profile_begin("hub.light", s);
     k_light_pairs<<<hb_grid((uint64_t)nM * 32, 256), 256, 0, s>>>(p.offM, ptr<uint32_t>(p.mR), ptr<uint32_t>(hd),
                                                                   nM, tau, hub0, h, ptr<unsigned int>(CL), light_n);
     count_launch();
+    profile_end("hub.light", s);
   }
   const uint64_t ntiles = (uint64_t)(h / TM) * (h / TM + 1) / 2;
   const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)sm_count_hub() * HB_PER_SM, ntiles);

@@ -78,12 +78,14 @@ def test_start_side_invariance(big):
 
 
 def test_hub_block_same_count(big):
-    """The tensor-core hub block (top 16,384 U ranks) in the benchmark's
-    configuration gives the walk's count."""
+    """The tensor-core hub block in the benchmark's configuration (automatic
+    hub set; and the top 16,384 U ranks) gives the walk's count."""
     g, G = big
     B, _ = G.exact()
     Bh, side, st = G.exact_hub()
-    assert side == 0 and st["hubs"] == 16384
+    assert side == 0 and 0 < st["hubs"] <= 16384 and st["hubs"] % 128 == 0
     assert 0 < st["K"] <= 65536 and st["light_pairs"] > 0
     assert Bh == B
+    Bh, _, st = G.exact_hub(hubs=16384)
+    assert Bh == B and st["hubs"] == 16384
     assert G.exact(hub_mma=True)[0] == B

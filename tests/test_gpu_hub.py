@@ -71,16 +71,19 @@ def test_biclique_closed_form(bfc):
                 assert B == want, (hubs, tau, st)
 
 
-def test_ragged_start_side_and_default_size(bfc):
-    """nS = 1000 is not a multiple of 128: the default hub set is the top 896
-    ranks; hubs = 0 on a side smaller than 128 falls back to the plain walk."""
+def test_ragged_start_side_and_automatic_size(bfc):
+    """nS = 1000 is not a multiple of 128: the largest hub set is the top 896
+    ranks.  The automatic size covers the walk's big class, which this small
+    uniform graph does not have (no hubs: the plain walk), as a side smaller
+    than 128 never has hubs."""
     u, v = synth.uniform_bipartite(1000, 100, 8000, 4)
     oB, _ = O.exact(u, v, 1000, 100)
     with bfc.Graph(u, v, 1000, 100) as G:
-        B, _, st = G.exact_hub("U")
+        B, _, st = G.exact_hub("U", hubs=896)
         assert B == oB and st["hubs"] == 896
-        B, _, st = G.exact_hub("V")
-        assert B == oB and st["hubs"] == 0
+        for side in ("U", "V"):
+            B, _, st = G.exact_hub(side)
+            assert B == oB and st["hubs"] == 0
         B, _ = G.exact("U", hub_mma=True)
         assert B == oB
 
