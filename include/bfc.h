@@ -226,6 +226,42 @@ int bfc_clrspar(bfc_graph *g, uint32_t colors, uint32_t trials, uint64_t seed, d
 int bfc_vsamp(bfc_graph *g, uint64_t k, const bfc_proposal *prop, uint32_t trials, uint64_t seed,
               double *est, uint64_t *drawn, uint64_t *bdraw, void *stream);
 
+/* ESamp (Algorithm 5): `trials` independent trials of k uniform edge draws.
+ * Draw j of trial t has seed ds = output j+1 of the SplitMix64 sequence
+ * seeded by s_t (s_t = output t+1 of `seed`'s sequence); its edge is
+ * canonical edge e = mulhi64(output 1 of ds, m) = (a, x), a in U.
+ *   reps == 0: the draw's value is b_e, computed exactly (Section 2's
+ *     definition: the edges between Gamma_x \ {a} and Gamma_a \ {x}), and its
+ *     term is b_e * m / 4.
+ *   reps > 0: Algorithm 7 in place of the exact count, repeated reps times:
+ *     repetition i takes the mulhi64(output 2i+2 of ds, d_x)-th entry a2 of x's
+ *     row and the mulhi64(output 2i+3 of ds, d_a)-th entry x2 of a's row (rows
+ *     ascending; full lists) and hits when a2 != a, x2 != x and (a2, x2) is an
+ *     edge.  Value = hits h; term = h * d_a * d_x / reps * m / 4.
+ *   est   (host, trials): the mean of each trial's k terms.
+ *   edges (device, trials * k, may be NULL): canonical edge of each draw.
+ *   vals  (device, trials * k, may be NULL): the draw's value.
+ * trials * k < 2^32.  Errors: BFC_EINVAL (m == 0, trials == 0, null est),
+ * BFC_ERANGE, BFC_ENOMEM, BFC_ECUDA. */
+int bfc_esamp(bfc_graph *g, uint64_t k, uint32_t reps, uint32_t trials, uint64_t seed, double *est,
+              uint64_t *edges, uint64_t *vals, void *stream);
+
+/* WSamp (Algorithm 6): `trials` trials of k wedge draws.  Population as in
+ * bfc_vsamp (index i < nU: U vertex i, else V vertex i - nU); h = sum_i
+ * C(d_i, 2), the number of wedges.  Draw j of trial t (seed ds as in
+ * bfc_esamp): the centre is the first i with C(d_0,2) + ... + C(d_i,2) >
+ * mulhi64(output 1 of ds, h) (the prefix-sum search of Section 5.3); with
+ * p = mulhi64(output 2, d_c) and q = mulhi64(output 3, d_c - 1), q += (q >= p),
+ * the endpoints are the p-th and q-th entries of the centre's row, and
+ * beta = |Gamma_v ^ Gamma_w| - 1; term = beta * h / 4.
+ *   est     (host, trials): the mean of each trial's k terms.
+ *   centres (device, trials * k, may be NULL): population index of each centre.
+ *   betas   (device, trials * k, may be NULL): beta of each draw.
+ * Errors: BFC_EINVAL (no wedge, trials == 0, null est), BFC_ERANGE,
+ * BFC_ENOMEM, BFC_ECUDA. */
+int bfc_wsamp(bfc_graph *g, uint64_t k, uint32_t trials, uint64_t seed, double *est, uint64_t *centres,
+              uint64_t *betas, void *stream);
+
 /* A sampling proposal from integer weights (device or host per flags
  * BFC_INPUT_DEVICE), one per population index (nU + nV entries, U first).
  * The weights are copied; W = sum must be > 0. */
@@ -249,8 +285,9 @@ int bfc_plan_stats(bfc_graph *g, int side, uint64_t *out, void *stream);
  * bfc_profile_read synchronises on the recorded events and returns, for the
  * kernel tag (e.g. "win.total", "warp.vertex", "big.edge"), the number of
  * launches and their summed device time in milliseconds.  Tags:
- * {warp,win,big}.{total,vertex,edge,single,local}, and for bfc_exact_hub
- * hub.total (the tensor-core tile kernel), hub.degree and hub.light. */
+ * {warp,win,big}.{total,vertex,edge,single,local}, for bfc_exact_hub
+ * hub.total (the tensor-core tile kernel), hub.degree and hub.light, and
+ * esamp.exact, esamp.fast and wsamp for the samplers. */
 int bfc_profile_enable(int on);
 int bfc_profile_reset(void);
 int bfc_profile_read(const char *tag, uint64_t *launches, double *total_ms);

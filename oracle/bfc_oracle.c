@@ -15,6 +15,8 @@
  *     the start set), run without the optional w < v ordering
  *   - vBFC: Algorithm 2;  eBFC: the definition of b_e (Section 2), see orc_per_edge
  *   - ESpar: Algorithm 8;  ClrSpar: Algorithm 9;  VSamp: Algorithm 4
+ *   - ESamp: Algorithm 5 (exact b_e per draw) and with Algorithm 7 (fast
+ *     per-edge estimate);  WSamp: Algorithm 6
  *
  * Conventions shared with the library interface (these are not arithmetic of
  * the method):
@@ -470,6 +472,156 @@ int orc_vsamp_trial(uint32_t nU, uint32_t nV, uint64_t m, const uint32_t *u, con
     }
     cmap_free(&c);
     free(prefix);
+    graph_free(&g);
+    *est = k ? acc / (double)k : 0.0;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* edge sampling (Algorithm 5) with exact per-edge counts or with the fast    */
+/* per-edge estimate of Algorithm 7                                          */
+/* ------------------------------------------------------------------------ */
+
+/* 1 iff (a, x) is an edge: binary search in U row a (ascending V ids). */
+static int has_edge(const graph *g, uint32_t a, uint32_t x) {
+    uint64_t lo = g->offU[a], hi = g->offU[a + 1];
+    while (lo < hi) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        if (g->nbrU[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo < g->offU[a + 1] && g->nbrU[lo] == x;
+}
+
+/* Draw j of trial t has its own seed ds = output j + 1 of the trial's
+ * sequence, and its edge is the canonical edge mulhi64(output 1 of ds, m),
+ * (a, x) with a in L.
+ *   reps == 0 (Algorithm 5 with exact counts): the draw's value is b_e
+ *     (Section 2 definition, ebfc) and its term b_e * m / 4.
+ *   reps > 0 (Algorithm 5 with Algorithm 7 in place of the exact count):
+ *     repetition i picks a2 = the mulhi64(output 2i + 2 of ds, d_x)-th L
+ *     neighbour of x and x2 = the mulhi64(output 2i + 3 of ds, d_a)-th R
+ *     neighbour of a, both from the full neighbour lists (rows ascending);
+ *     it is a hit when a2 != a, x2 != x and (a2, x2) is an edge, i.e. when
+ *     a, x, a2, x2 form a butterfly.  The draw's value is the hit count h,
+ *     its estimate of b_e is h * d_a * d_x / reps, and its term that times m / 4.
+ * The trial estimate is the mean of the k terms.  edges[j] / vals[j]
+ * (optional) receive the canonical edge id and the draw's value. */
+int orc_esamp_trial(uint32_t nU, uint32_t nV, uint64_t m, const uint32_t *u, const uint32_t *v, uint64_t k,
+                    uint32_t reps, uint64_t seed, uint32_t t, double *est, uint64_t *edges, uint64_t *vals) {
+    if (m == 0) return -2;
+    graph g;
+    int rc = graph_build(nU, nV, m, u, v, &g);
+    if (rc) return rc;
+    uint8_t *mark = (uint8_t *)calloc((size_t)nU + 1, 1);
+    if (!mark) { graph_free(&g); return -1; }
+    uint64_t ts = trial_seed(seed, t);
+    double acc = 0.0;
+    for (uint64_t j = 0; j < k; j++) {
+        uint64_t ds = orc_splitmix64(ts, j + 1);
+        uint64_t e = mulhi64(orc_splitmix64(ds, 1), m);
+        /* the L end of canonical edge e: the row that holds position e */
+        uint32_t lo = 0, hi = nU - 1;
+        while (lo < hi) {
+            uint32_t mid = lo + (hi - lo + 1) / 2;
+            if (g.offU[mid] <= e) lo = mid; else hi = mid - 1;
+        }
+        uint32_t a = lo, x = g.nbrU[e];
+        uint64_t val;
+        double term;
+        if (reps == 0) {
+            val = ebfc(&g, a, x, mark);
+            term = (double)val * (double)m / 4.0;
+        } else {
+            uint64_t da = g.offU[a + 1] - g.offU[a], dx = g.offV[x + 1] - g.offV[x];
+            uint64_t hits = 0;
+            for (uint32_t i = 0; i < reps; i++) {
+                uint32_t a2 = g.nbrV[g.offV[x] + mulhi64(orc_splitmix64(ds, 2 * (uint64_t)i + 2), dx)];
+                uint32_t x2 = g.nbrU[g.offU[a] + mulhi64(orc_splitmix64(ds, 2 * (uint64_t)i + 3), da)];
+                if (a2 != a && x2 != x && has_edge(&g, a2, x2)) hits++;
+            }
+            val = hits;
+            term = (double)hits * (double)da * (double)dx / (double)reps * (double)m / 4.0;
+        }
+        acc += term;
+        if (edges) edges[j] = e;
+        if (vals) vals[j] = val;
+    }
+    free(mark);
+    graph_free(&g);
+    *est = k ? acc / (double)k : 0.0;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* wedge sampling (Algorithm 6)                                              */
+/* ------------------------------------------------------------------------ */
+
+/* Population as in VSamp: index i < nU is L vertex i, else R vertex i - nU;
+ * h = sum_i C(d_i, 2), the number of wedges.  Draw j of trial t, with
+ * ds = output j + 1 of the trial's sequence:
+ *   centre c = the first i with C(d_0, 2) + ... + C(d_i, 2) > mulhi64(output 1 of ds, h)
+ *     (probability C(d_c, 2) / h);
+ *   endpoints: p = mulhi64(output 2 of ds, d_c), q = mulhi64(output 3 of ds, d_c - 1),
+ *     q' = q + (q >= p); v, w = the p-th and q'-th neighbours of c (rows
+ *     ascending), two distinct neighbours with every unordered pair equally likely;
+ *   beta = |Gamma_v ^ Gamma_w| - 1, the butterflies that contain the wedge;
+ *   term = beta * h / 4.
+ * The trial estimate is the mean of the k terms.  centres[j] / betas[j]
+ * (optional) receive the centre's population index and beta. */
+int orc_wsamp_trial(uint32_t nU, uint32_t nV, uint64_t m, const uint32_t *u, const uint32_t *v, uint64_t k,
+                    uint64_t seed, uint32_t t, double *est, uint64_t *centres, uint64_t *betas) {
+    graph g;
+    int rc = graph_build(nU, nV, m, u, v, &g);
+    if (rc) return rc;
+    uint64_t n = (uint64_t)nU + nV;
+    uint64_t *prefix = (uint64_t *)malloc((n ? n : 1) * sizeof(uint64_t));
+    uint8_t *mark = (uint8_t *)calloc((size_t)(nU > nV ? nU : nV) + 1, 1);
+    if (!prefix || !mark) { free(prefix); free(mark); graph_free(&g); return -1; }
+    u128 h = 0;
+    for (uint64_t i = 0; i < n; i++) {
+        int s = i < nU ? 0 : 1;
+        uint32_t id = (uint32_t)(s ? i - nU : i);
+        const uint64_t *off = side_off(&g, s);
+        uint64_t d = off[id + 1] - off[id];
+        h += (u128)d * (d ? d - 1 : 0) / 2;
+        if (h >> 64) { free(prefix); free(mark); graph_free(&g); return -5; }
+        prefix[i] = (uint64_t)h;
+    }
+    if (h == 0) { free(prefix); free(mark); graph_free(&g); return -2; }
+    uint64_t ts = trial_seed(seed, t);
+    double acc = 0.0;
+    for (uint64_t j = 0; j < k; j++) {
+        uint64_t ds = orc_splitmix64(ts, j + 1);
+        uint64_t target = mulhi64(orc_splitmix64(ds, 1), (uint64_t)h);
+        uint64_t lo = 0, hi = n - 1;       /* first i with prefix[i] > target */
+        while (lo < hi) {
+            uint64_t mid = lo + (hi - lo) / 2;
+            if (prefix[mid] > target) hi = mid; else lo = mid + 1;
+        }
+        int s = lo < nU ? 0 : 1;
+        uint32_t c = (uint32_t)(s ? lo - nU : lo);
+        const uint64_t *off = side_off(&g, s);
+        const uint32_t *nbr = side_nbr(&g, s);
+        uint64_t d = off[c + 1] - off[c];
+        uint64_t p = mulhi64(orc_splitmix64(ds, 2), d);
+        uint64_t q = mulhi64(orc_splitmix64(ds, 3), d - 1);
+        if (q >= p) q++;
+        uint32_t a = nbr[off[c] + p], b = nbr[off[c] + q];
+        /* a and b are on the other side: intersect their rows */
+        int o = 1 - s;
+        const uint64_t *ooff = side_off(&g, o);
+        const uint32_t *onbr = side_nbr(&g, o);
+        for (uint64_t i = ooff[a]; i < ooff[a + 1]; i++) mark[onbr[i]] = 1;
+        uint64_t common = 0;
+        for (uint64_t i = ooff[b]; i < ooff[b + 1]; i++) common += mark[onbr[i]];
+        for (uint64_t i = ooff[a]; i < ooff[a + 1]; i++) mark[onbr[i]] = 0;
+        uint64_t beta = common - 1;        /* c itself is common to both */
+        acc += (double)beta * (double)(uint64_t)h / 4.0;
+        if (centres) centres[j] = lo;
+        if (betas) betas[j] = beta;
+    }
+    free(prefix);
+    free(mark);
     graph_free(&g);
     *est = k ? acc / (double)k : 0.0;
     return 0;

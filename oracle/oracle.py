@@ -10,6 +10,9 @@ Paper references (arXiv 1801.00338):
   * Section 2: butterfly, b_e definitions; Algorithm 3: eBFC (see bfc_oracle.c)
   * Algorithm 4 / Lemma 4: VSamp; Algorithm 8 / Lemma 8: ESpar;
     Algorithm 9 / Lemma 9: ClrSpar; Section 5: butterfly pair types
+  * Algorithm 5: ESamp (exact b_e per draw); Algorithm 7: the fast per-edge
+    estimate used in its place; Algorithm 6: WSamp (Section 5.3 for the
+    prefix-sum centre draw)
 """
 from __future__ import annotations
 
@@ -55,13 +58,16 @@ def lib():
         L.orc_espar_trial.argtypes = [u32, u32, u64, P, P, u32, u64, u32, P, P]
         L.orc_clrspar_trial.argtypes = [u32, u32, u64, P, P, u32, u64, u32, P, P]
         L.orc_vsamp_trial.argtypes = [u32, u32, u64, P, P, u64, P, u64, u32, P, P, P]
+        L.orc_esamp_trial.argtypes = [u32, u32, u64, P, P, u64, u32, u64, u32, P, P, P]
+        L.orc_wsamp_trial.argtypes = [u32, u32, u64, P, P, u64, u64, u32, P, P, P]
         L.orc_prepare.argtypes = [u32, u32, u64, P, P, i32]
         L.orc_prepare.restype = P
         L.orc_prepared_count.argtypes = [P, u64, P, P, P]
         L.orc_prepared_free.argtypes = [P]
         for f in ("orc_degree_square_sums", "orc_exact", "orc_per_vertex", "orc_per_vertex_list",
                   "orc_per_edge", "orc_per_edge_list", "orc_canonical_ids", "orc_espar_trial",
-                  "orc_clrspar_trial", "orc_vsamp_trial", "orc_prepared_count"):
+                  "orc_clrspar_trial", "orc_vsamp_trial", "orc_esamp_trial", "orc_wsamp_trial",
+                  "orc_prepared_count"):
             getattr(L, f).restype = i32
         _lib = L
     return _lib
@@ -203,6 +209,34 @@ def vsamp_trial(u, v, nU, nV, k: int, seed: int, t: int, weights=None):
     return float(est[0]), drawn[:k], bd[:k]
 
 
+def esamp_trial(u, v, nU, nV, k: int, reps: int, seed: int, t: int):
+    """One ESamp trial of k edge draws (Algorithm 5).  reps = 0: exact b_e per
+    draw; reps > 0: Algorithm 7 repeated reps times per draw.
+
+    Returns (estimate, canonical edge ids drawn, value of each draw: b_e or
+    the hit count)."""
+    u, v, pu, pv = _edges(u, v)
+    est = np.zeros(1, np.float64)
+    edges = np.zeros(max(k, 1), np.uint64)
+    vals = np.zeros(max(k, 1), np.uint64)
+    _check(lib().orc_esamp_trial(nU, nV, u.size, pu, pv, k, reps, seed & 0xFFFFFFFFFFFFFFFF, t,
+                                 est.ctypes.data, edges.ctypes.data, vals.ctypes.data), "esamp")
+    return float(est[0]), edges[:k], vals[:k]
+
+
+def wsamp_trial(u, v, nU, nV, k: int, seed: int, t: int):
+    """One WSamp trial of k wedge draws (Algorithm 6).
+
+    Returns (estimate, population index of each centre, beta of each draw)."""
+    u, v, pu, pv = _edges(u, v)
+    est = np.zeros(1, np.float64)
+    cen = np.zeros(max(k, 1), np.uint64)
+    beta = np.zeros(max(k, 1), np.uint64)
+    _check(lib().orc_wsamp_trial(nU, nV, u.size, pu, pv, k, seed & 0xFFFFFFFFFFFFFFFF, t,
+                                 est.ctypes.data, cen.ctypes.data, beta.ctypes.data), "wsamp")
+    return float(est[0]), cen[:k], beta[:k]
+
+
 class Prepared:
     """A graph prepared once, for timing Algorithm 1's per-start-vertex loops."""
 
@@ -317,6 +351,43 @@ def vsamp_variance(b_all: np.ndarray, q: np.ndarray | None = None) -> float:
         q = np.full(n, 1.0 / n)
     B = b.sum() / 4.0
     return float(np.sum(b * b / (16.0 * q)) - B * B)
+
+
+def wedges(u, v, nU, nV):
+    """Every wedge of the graph, by enumeration (tiny graphs): a list of
+    (centre population index, endpoint, endpoint, beta) with the endpoints an
+    unordered pair of distinct neighbours of the centre and beta = the number
+    of butterflies that contain the wedge (common neighbours of the endpoints
+    other than the centre)."""
+    u = np.asarray(u, np.int64)
+    v = np.asarray(v, np.int64)
+    nb = [[set() for _ in range(nU)], [set() for _ in range(nV)]]
+    for a, x in zip(u.tolist(), v.tolist()):
+        nb[0][a].add(x)
+        nb[1][x].add(a)
+    out = []
+    for s, n in ((0, nU), (1, nV)):
+        for c in range(n):
+            for p, q in itertools.combinations(sorted(nb[s][c]), 2):
+                common = nb[1 - s][p] & nb[1 - s][q]
+                out.append((c if s == 0 else nU + c, p, q, len(common) - 1))
+    return out
+
+
+def esamp_term_variance(be: np.ndarray, dA: np.ndarray, dX: np.ndarray, reps: int) -> float:
+    """Exact variance of one ESamp term (Algorithm 5): with exact counts
+    (reps = 0) the term is b_e m / 4 for a uniform edge e; with Algorithm 7
+    repeated reps times it is (m / 4) d_a d_x h / reps, h ~ Binomial(reps,
+    b_e / (d_a d_x)) given e, which adds E_e[(m/4)^2 (b_e d_a d_x - b_e^2) / reps]
+    (Lemma on Algorithm 7: Var = b_e d_a d_x - b_e^2 for one repetition)."""
+    b = np.asarray(be, np.float64)
+    m = b.size
+    B = b.sum() / 4.0
+    var = (m / 16.0) * np.sum(b * b) - B * B
+    if reps:
+        dd = np.asarray(dA, np.float64) * np.asarray(dX, np.float64)
+        var += (m / 16.0) * np.sum(b * dd - b * b) / reps
+    return float(var)
 
 
 def mixture_q(weights: np.ndarray) -> np.ndarray:

@@ -62,6 +62,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "bfc_espar": [P, dbl, u32, u64, P, P, P],
         "bfc_clrspar": [P, u32, u32, u64, P, P, P],
         "bfc_vsamp": [P, u64, P, u32, u64, P, P, P, P],
+        "bfc_esamp": [P, u64, u32, u32, u64, P, P, P, P],
+        "bfc_wsamp": [P, u64, u32, u64, P, P, P, P],
         "bfc_proposal_from_weights": [P, P, u32, P, P],
         "bfc_proposal_free": [P],
         "bfc_exact_csr_noalloc": [P, P, u32, P, P, u32, u32, P, P],
@@ -155,7 +157,7 @@ def bfc_profile_read(tag: str) -> tuple[int, float]:
 
 
 PROFILE_TAGS = [f"{c}.{m}" for c in ("warp", "win", "big") for m in ("total", "vertex", "edge", "single", "local")]
-PROFILE_TAGS += ["hub.total", "hub.degree", "hub.light"]
+PROFILE_TAGS += ["hub.total", "hub.degree", "hub.light", "esamp.exact", "esamp.fast", "wsamp"]
 # kernel tag -> the classes it runs
 TAG_CLASSES = {"warp": ("warp",), "win": ("s2", "s4", "s8", "s16", "s32", "l2", "l4", "l8", "l16", "l32"),
                "big": ("big",)}
@@ -304,6 +306,43 @@ def bfc_vsamp(h: int, k: int, trials: int, seed: int, proposal: int | None = Non
     return est
 
 
+def bfc_esamp(h: int, k: int, reps: int, trials: int, seed: int, want_draws: bool = False, stream=None):
+    """ESamp (Algorithm 5): per-trial estimates; with want_draws also the
+    device arrays of drawn canonical edges and of the draws' values (b_e, or
+    Algorithm 7's hit counts when reps > 0)."""
+    import torch
+    est = np.zeros(trials, np.float64)
+    ed = vd = None
+    pe = pv = None
+    if want_draws:
+        ed = torch.empty(max(trials * k, 1), dtype=torch.int64, device="cuda")
+        vd = torch.empty(max(trials * k, 1), dtype=torch.int64, device="cuda")
+        pe, pv = _dptr(ed), _dptr(vd)
+    _check(load().bfc_esamp(h, k, reps, trials, seed & 0xFFFFFFFFFFFFFFFF, est.ctypes.data, pe, pv,
+                            _stream_ptr(stream)), "bfc_esamp")
+    if want_draws:
+        return est, ed[: trials * k], vd[: trials * k]
+    return est
+
+
+def bfc_wsamp(h: int, k: int, trials: int, seed: int, want_draws: bool = False, stream=None):
+    """WSamp (Algorithm 6): per-trial estimates; with want_draws also the
+    device arrays of centres (population index) and betas."""
+    import torch
+    est = np.zeros(trials, np.float64)
+    cd = bd = None
+    pc = pb = None
+    if want_draws:
+        cd = torch.empty(max(trials * k, 1), dtype=torch.int64, device="cuda")
+        bd = torch.empty(max(trials * k, 1), dtype=torch.int64, device="cuda")
+        pc, pb = _dptr(cd), _dptr(bd)
+    _check(load().bfc_wsamp(h, k, trials, seed & 0xFFFFFFFFFFFFFFFF, est.ctypes.data, pc, pb, _stream_ptr(stream)),
+           "bfc_wsamp")
+    if want_draws:
+        return est, cd[: trials * k], bd[: trials * k]
+    return est
+
+
 MLP_FEATURES = 6
 MLP_PARAMS = 4673
 
@@ -433,6 +472,12 @@ class Graph:
 
     def vsamp(self, k, trials, seed, proposal=None, want_draws=False, stream=None):
         return bfc_vsamp(self.h, k, trials, seed, proposal, want_draws, stream)
+
+    def esamp(self, k, trials, seed, reps=0, want_draws=False, stream=None):
+        return bfc_esamp(self.h, k, reps, trials, seed, want_draws, stream)
+
+    def wsamp(self, k, trials, seed, want_draws=False, stream=None):
+        return bfc_wsamp(self.h, k, trials, seed, want_draws, stream)
 
     def close(self):
         if self.h:

@@ -176,6 +176,10 @@ int plan_classify_device(Plan &p, uint32_t *cls_of, unsigned int *dev, unsigned 
 int wedge_count_device_lists(bfc_graph *g, Plan &p, const unsigned int *dev, uint32_t big_cap,
                              unsigned long long *d_B, cudaStream_t s);
 void plan_free(Plan &p, cudaStream_t s);
+// b_x = 1/2 sum of b_e over the rows off[x] .. off[x+1] (Lemma 1's identity
+// for one vertex); eid: canonical id of each row entry, or null for identity.
+int vertex_from_edges(const uint64_t *off, uint32_t n, const uint32_t *eid, const uint64_t *be, uint64_t *out,
+                      cudaStream_t s);
 // TOTAL mode over start ranks < rank_end only (ranks >= rank_end walk nothing).
 int wedge_count_below(bfc_graph *g, Plan &p, uint32_t rank_end, unsigned long long *d_B, cudaStream_t s);
 

@@ -165,28 +165,26 @@ static int whole_rows(bfc_graph *g, uint32_t flags, uint64_t *bU, uint64_t *bV, 
   return BFC_OK;
 }
 
-// The ordered one-sided sweep: per-vertex outputs (both sides) and/or per-edge outputs.
+// The ordered one-sided sweep (each pair once, Algorithm 1's order) in EDGE
+// mode: b_e for every edge (both edges of every counted wedge pair are
+// credited), then b_x = 1/2 sum_{e containing x} b_e on both sides.
 static int ordered_local(bfc_graph *g, uint32_t flags, uint64_t *bU, uint64_t *bV, uint64_t *be, uint64_t *out_B,
                          cudaStream_t s) {
   int side = 0;
   BFC_TRY(prepare(g, flags, s, &side));
-  if (be && g->m > 0) BFC_CUDA_TRY(cudaMemsetAsync(be, 0, g->m * 8, s));
-  if (!bU && !bV) {
-    BFC_TRY(wedge_count(g, g->plan[side], MODE_EDGE, acc_B(g), nullptr, nullptr, be, s));
-    return finish_count(g, out_B, s);
+  DBuf tmpE;
+  uint64_t *pe = be;
+  if (!pe && g->m > 0) {
+    BFC_TRY(dalloc(tmpE, g->m * 8, s));
+    pe = ptr<uint64_t>(tmpE);
   }
-  DBuf tmpU, tmpV;
   int rc = BFC_OK;
-  if (!bU) rc = dalloc(tmpU, (uint64_t)g->nU * 8, s);
-  if (!rc && !bV) rc = dalloc(tmpV, (uint64_t)g->nV * 8, s);
-  uint64_t *pU = bU ? bU : ptr<uint64_t>(tmpU);
-  uint64_t *pV = bV ? bV : ptr<uint64_t>(tmpV);
-  if (!rc && cudaMemsetAsync(pU, 0, (uint64_t)g->nU * 8, s) != cudaSuccess) rc = BFC_ECUDA;
-  if (!rc && cudaMemsetAsync(pV, 0, (uint64_t)g->nV * 8, s) != cudaSuccess) rc = BFC_ECUDA;
-  if (!rc) rc = wedge_count(g, g->plan[side], MODE_VERTEX, acc_B(g), side ? pV : pU, side ? pU : pV, be, s);
+  if (g->m > 0 && cudaMemsetAsync(pe, 0, g->m * 8, s) != cudaSuccess) rc = BFC_ECUDA;
+  if (!rc) rc = wedge_count(g, g->plan[side], MODE_EDGE, acc_B(g), nullptr, nullptr, pe, s);
+  if (!rc && bU) rc = vertex_from_edges(ptr<uint64_t>(g->offU), g->nU, nullptr, pe, bU, s);
+  if (!rc && bV) rc = vertex_from_edges(ptr<uint64_t>(g->offV), g->nV, ptr<uint32_t>(g->eidV), pe, bV, s);
   if (!rc) rc = finish_count(g, out_B, s);
-  dfree(tmpU, s);
-  dfree(tmpV, s);
+  dfree(tmpE, s);
   return rc;
 }
 

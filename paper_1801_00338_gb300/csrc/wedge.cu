@@ -1054,6 +1054,31 @@ int wedge_local(bfc_graph *g, Plan &p, unsigned long long *d_2B, uint64_t *bS, u
   return BFC_OK;
 }
 
+// b_x = 1/2 sum_{e containing x} b_e (every butterfly through x holds two of
+// x's edges) over the rows off[x] .. off[x+1]; eid maps row entries to
+// canonical edge ids (null: the row entries are the canonical ids)
+__global__ void k_half_row_sums(const uint64_t *off, uint32_t n, const uint32_t *eid, const unsigned long long *be,
+                                unsigned long long *out) {
+  const int lane = threadIdx.x & 31;
+  uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t x = warp; x < n; x += nw) {
+    uint64_t t = 0;
+    for (uint64_t i = off[x] + lane; i < off[x + 1]; i += 32) t += be[eid ? eid[i] : i];
+    t = warp_sum_u64(t);
+    if (lane == 0) out[x] = t / 2;
+  }
+}
+
+int vertex_from_edges(const uint64_t *off, uint32_t n, const uint32_t *eid, const uint64_t *be, uint64_t *out,
+                      cudaStream_t s) {
+  if (n == 0) return BFC_OK;
+  k_half_row_sums<<<grid_for((uint64_t)n * 32, 256), 256, 0, s>>>(
+      off, n, eid, reinterpret_cast<const unsigned long long *>(be), reinterpret_cast<unsigned long long *>(out));
+  BFC_LAUNCHED();
+  return BFC_OK;
+}
+
 // move the staged sums to their outputs: be[canonical id] += beM[row entry],
 // bS[vertex id] += bSr[rank]
 __global__ void k_finish_edges(const uint32_t *mEid, uint64_t m, const unsigned long long *beM,

@@ -89,3 +89,19 @@ def test_hub_block_same_count(big):
     Bh, _, st = G.exact_hub(hubs=16384)
     assert Bh == B and st["hubs"] == 16384
     assert G.exact(hub_mma=True)[0] == B
+
+
+def test_samplers_draws_match_oracle(big):
+    """ESamp (exact and with Algorithm 7, 1,000 repetitions) and WSamp on the
+    full graph: every drawn edge / centre and the integer value of every draw
+    equal the oracle's, computed draw by draw."""
+    g, G = big
+    for reps, k in ((0, 60), (1000, 200)):
+        est, ed, vd = G.esamp(k, 1, 99, reps=reps, want_draws=True)
+        oe, oed, ovd = O.esamp_trial(g.u, g.v, g.nU, g.nV, k, reps, 99, 0)
+        assert np.array_equal(u64(ed), oed) and np.array_equal(u64(vd), ovd)
+        assert est[0] == pytest.approx(oe, rel=1e-12)
+    est, cd, bd = G.wsamp(300, 1, 98, want_draws=True)
+    oe, ocd, obd = O.wsamp_trial(g.u, g.v, g.nU, g.nV, 300, 98, 0)
+    assert np.array_equal(u64(cd), ocd) and np.array_equal(u64(bd), obd)
+    assert est[0] == pytest.approx(oe, rel=1e-12)

@@ -359,3 +359,177 @@ def test_vsamp_mean_of_trials_within_3_se():
     assert abs(np.mean(ests) - B) <= 3 * math.sqrt(var / 1000)
     # the sample variance of the trials agrees with the exact one
     assert np.var(ests) == pytest.approx(var, rel=0.15)
+
+
+# ----------------------------------------------------------------------------
+# edge sampling (Algorithm 5) and the fast per-edge estimate (Algorithm 7)
+# ----------------------------------------------------------------------------
+
+def _dense(nU, nV, p, seed):
+    r = synth.uniform01(seed, 0, nU * nV).reshape(nU, nV)
+    a, x = np.nonzero(r < p)
+    return a.astype(np.uint32), x.astype(np.uint32)
+
+
+def _adj(u, v, nU, nV):
+    rows = [sorted(v[u == a].tolist()) for a in range(nU)]
+    cols = [sorted(u[v == x].tolist()) for x in range(nV)]
+    return rows, cols
+
+
+def test_esamp_second_moment_matches_pair_types():
+    """Var of Algorithm 5's term is (m/16) sum_e b_e^2 - B^2, and
+    sum_e b_e^2 = 4B + 2 p_1e + 4 p_1w (ordered pairs of distinct butterflies
+    sharing one edge or two): b_e from the definition against the brute-force
+    pair classification; the paper's bound Var <= (m/4)(B + p_E) holds."""
+    for seed in (1, 2, 3):
+        u, v = _dense(7, 8, 0.55, seed)
+        B, _ = O.exact(u, v, 7, 8)
+        be = O.per_edge(u, v, 7, 8).astype(np.float64)
+        pairs = O.pair_types(u, v)
+        assert len(O.butterflies(u, v)) == B
+        assert be.sum() == 4 * B
+        assert int((be * be).sum()) == 4 * B + 2 * pairs["1e"] + 4 * pairs["1w"]
+        m = u.size
+        var = O.esamp_term_variance(be, None, None, 0)
+        assert var == pytest.approx(m / 16.0 * (4 * B + 2 * pairs["1e"] + 4 * pairs["1w"]) - B * B, rel=1e-12)
+        assert var <= m / 4.0 * (B + pairs["1e"] + pairs["1w"])
+
+
+def test_fast_ebfc_expectation_by_enumeration():
+    """Algorithm 7 on edge (a, x): over all d_x * d_a equally likely choices of
+    a2 in Gamma_x and x2 in Gamma_a (full lists, a2 = a or x2 = x a miss), the
+    hits are exactly the butterflies through the edge, so E[Y] = b_e; one
+    repetition has variance b_e d_a d_x - b_e^2 <= b_e d_a d_x."""
+    u, v = _dense(8, 7, 0.5, 4)
+    rows, cols = _adj(u, v, 8, 7)
+    E = set(zip(u.tolist(), v.tolist()))
+    be = O.per_edge(u, v, 8, 7)
+    bf = O.butterflies(u, v)
+    for i, (a, x) in enumerate(zip(u.tolist(), v.tolist())):
+        hits = sum(1 for a2 in cols[x] for x2 in rows[a] if a2 != a and x2 != x and (a2, x2) in E)
+        assert hits == be[i]
+        assert hits == sum(1 for (p, q, y, z) in bf if a in (p, q) and x in (y, z))
+        dd = len(rows[a]) * len(cols[x])
+        mean = hits / dd * dd
+        second = hits / dd * dd * dd
+        assert second - mean * mean == pytest.approx(be[i] * dd - be[i] ** 2)
+
+
+def test_esamp_draws_recomputed():
+    """The oracle's draw rule recomputed with Python integers: the edge of draw
+    j, and for Algorithm 7 the two neighbour picks of every repetition."""
+    nU, nV = 9, 10
+    u, v = _dense(nU, nV, 0.5, 5)
+    m = u.size
+    order = np.lexsort((v, u))
+    cu, cv = u[order].tolist(), v[order].tolist()   # canonical order
+    rows, cols = _adj(u, v, nU, nV)
+    E = set(zip(cu, cv))
+    be = O.per_edge(u, v, nU, nV)[order]
+    k, reps, seed, t = 12, 7, 77, 3
+    ts = int(synth.splitmix64(seed, t, 1)[0])
+    for r in (0, reps):
+        est, edges, vals = O.esamp_trial(u, v, nU, nV, k, r, seed, t)
+        terms = []
+        for j in range(k):
+            ds = int(synth.splitmix64(ts, j, 1)[0])
+            out = [int(z) for z in synth.splitmix64(ds, 0, 2 * r + 3)]
+            e = (out[0] * m) >> 64
+            assert int(edges[j]) == e
+            a, x = cu[e], cv[e]
+            if r == 0:
+                assert int(vals[j]) == be[e]
+                terms.append(be[e] * m / 4.0)
+            else:
+                da, dx = len(rows[a]), len(cols[x])
+                h = 0
+                for i in range(r):
+                    a2 = cols[x][(out[2 * i + 1] * dx) >> 64]
+                    x2 = rows[a][(out[2 * i + 2] * da) >> 64]
+                    h += a2 != a and x2 != x and (a2, x2) in E
+                assert int(vals[j]) == h
+                terms.append(h * da * dx / r * m / 4.0)
+        assert est == pytest.approx(np.mean(terms), rel=1e-12)
+
+
+@pytest.mark.parametrize("reps", [0, 10])
+def test_esamp_mean_of_trials_within_3_se(reps):
+    nU, nV = 12, 14
+    u, v = _dense(nU, nV, 0.45, 6)
+    B, _ = O.exact(u, v, nU, nV)
+    be = O.per_edge(u, v, nU, nV)
+    dA = np.bincount(u, minlength=nU)[u]
+    dX = np.bincount(v, minlength=nV)[v]
+    k, T = 5, 1000
+    ests = [O.esamp_trial(u, v, nU, nV, k, reps, 11, t)[0] for t in range(T)]
+    var = O.esamp_term_variance(be, dA, dX, reps) / k
+    assert abs(np.mean(ests) - B) <= 3 * math.sqrt(var / T)
+    assert np.var(ests) == pytest.approx(var, rel=0.15)
+
+
+# ----------------------------------------------------------------------------
+# wedge sampling (Algorithm 6)
+# ----------------------------------------------------------------------------
+
+def test_wsamp_moments_by_wedge_enumeration():
+    """Over all h wedges (both sides as centres): sum beta = 4B (each butterfly
+    has four wedges) and sum beta^2 = 4B + 2 p_1w (ordered pairs sharing a
+    wedge), so Var of one term (h/16) sum beta^2 - B^2 stays within the
+    paper's bound (h/4)(B + p_1w)."""
+    for seed in (7, 8):
+        u, v = _dense(7, 9, 0.5, seed)
+        B, _ = O.exact(u, v, 7, 9)
+        W = O.wedges(u, v, 7, 9)
+        dU = np.bincount(u, minlength=7)
+        dV = np.bincount(v, minlength=9)
+        h = int((dU * (dU - 1) // 2).sum() + (dV * (dV - 1) // 2).sum())
+        assert len(W) == h
+        beta = np.array([w[3] for w in W], np.int64)
+        pairs = O.pair_types(u, v)
+        assert beta.sum() == 4 * B
+        assert int((beta * beta).sum()) == 4 * B + 2 * pairs["1w"]
+        var = h / 16.0 * (beta * beta).sum() - B * B
+        assert var <= h / 4.0 * (B + pairs["1w"])
+
+
+def test_wsamp_draws_recomputed():
+    nU, nV = 8, 11
+    u, v = _dense(nU, nV, 0.45, 9)
+    rows, cols = _adj(u, v, nU, nV)
+    adj = rows + cols
+    d = np.array([len(r) for r in adj], np.int64)
+    c2 = d * (d - 1) // 2
+    pref = np.cumsum(c2)
+    h = int(pref[-1])
+    k, seed, t = 30, 5, 2
+    est, cen, beta = O.wsamp_trial(u, v, nU, nV, k, seed, t)
+    ts = int(synth.splitmix64(seed, t, 1)[0])
+    terms = []
+    for j in range(k):
+        ds = int(synth.splitmix64(ts, j, 1)[0])
+        r1, r2, r3 = (int(z) for z in synth.splitmix64(ds, 0, 3))
+        c = int(np.searchsorted(pref, (r1 * h) >> 64, side="right"))
+        p = (r2 * int(d[c])) >> 64
+        q = (r3 * (int(d[c]) - 1)) >> 64
+        q += q >= p
+        a, b = adj[c][p], adj[c][q]
+        other = cols if c < nU else rows
+        bt = len(set(other[a]) & set(other[b])) - 1
+        assert int(cen[j]) == c and int(beta[j]) == bt
+        terms.append(bt * h / 4.0)
+    assert est == pytest.approx(np.mean(terms), rel=1e-12)
+
+
+def test_wsamp_mean_of_trials_within_3_se():
+    nU, nV = 12, 13
+    u, v = _dense(nU, nV, 0.4, 10)
+    B, _ = O.exact(u, v, nU, nV)
+    W = O.wedges(u, v, nU, nV)
+    h = len(W)
+    beta = np.array([w[3] for w in W], np.float64)
+    var1 = h / 16.0 * (beta * beta).sum() - B * B
+    k, T = 5, 1000
+    ests = [O.wsamp_trial(u, v, nU, nV, k, 21, t)[0] for t in range(T)]
+    assert abs(np.mean(ests) - B) <= 3 * math.sqrt(var1 / k / T)
+    assert np.var(ests) == pytest.approx(var1 / k, rel=0.15)
