@@ -283,9 +283,9 @@ int bfc_plan_stats(bfc_graph *g, int side, uint64_t *out, void *stream);
 /* Device timing of the library's counting kernels: when enabled, every
  * wedge-kernel launch is bracketed by CUDA events on the launch stream.
  * bfc_profile_read synchronises on the recorded events and returns, for the
- * kernel tag (e.g. "win.total", "warp.vertex", "big.edge"), the number of
+ * kernel tag (e.g. "win.total", "warp.edge", "big.edge"), the number of
  * launches and their summed device time in milliseconds.  Tags:
- * {warp,win,big}.{total,vertex,edge,single,local}, for bfc_exact_hub
+ * {warp,win,big}.{total,edge,single,local}, for bfc_exact_hub
  * hub.total (the tensor-core tile kernel), hub.degree and hub.light, and
  * esamp.exact, esamp.fast and wsamp for the samplers. */
 int bfc_profile_enable(int on);

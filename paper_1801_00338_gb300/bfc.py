@@ -156,7 +156,7 @@ def bfc_profile_read(tag: str) -> tuple[int, float]:
     return int(n.value), float(ms.value)
 
 
-PROFILE_TAGS = [f"{c}.{m}" for c in ("warp", "win", "big") for m in ("total", "vertex", "edge", "single", "local")]
+PROFILE_TAGS = [f"{c}.{m}" for c in ("warp", "win", "big") for m in ("total", "edge", "single", "local")]
 PROFILE_TAGS += ["hub.total", "hub.degree", "hub.light", "esamp.exact", "esamp.fast", "wsamp"]
 # kernel tag -> the classes it runs
 TAG_CLASSES = {"warp": ("warp",), "win": ("s2", "s4", "s8", "s16", "s32", "l2", "l4", "l8", "l16", "l32"),

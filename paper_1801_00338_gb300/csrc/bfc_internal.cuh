@@ -145,7 +145,6 @@ struct bfc_graph {
   bfc::Plan plan[2];
   bfc::Scratch scr;
   bfc::DBuf beM;               // u64[m]  per-edge partial sums in midpoint-row order
-  bfc::DBuf bSr;               // u64[nS] per-vertex partial sums in rank order
   bfc::DBuf err;               // u32 device error word
   bfc::DBuf acc;               // u64 accumulators (small)
   cudaStream_t last_stream = nullptr;
@@ -158,12 +157,11 @@ int choose_side(const bfc_graph *g, uint32_t flags);
 int read_device_error(bfc_graph *g, cudaStream_t s);  // maps DERR_* bits to a status and clears
 
 // wedge.cu
-enum Mode { MODE_TOTAL = 0, MODE_VERTEX = 1, MODE_EDGE = 2, MODE_SINGLE = 3, MODE_LOCAL = 4 };
-// Counts with the start side of plan p.  out_B receives B (device u64).
-// bS / bM: per-vertex outputs of the start / midpoint side (device, original
-// ids) or null; be: per-edge output (canonical ids) or null.
-int wedge_count(bfc_graph *g, Plan &p, Mode mode, unsigned long long *d_B, uint64_t *bS, uint64_t *bM,
-                uint64_t *be, cudaStream_t s);
+enum Mode { MODE_TOTAL = 0, MODE_EDGE = 1, MODE_SINGLE = 2, MODE_LOCAL = 3 };
+// Counts with the start side of plan p (Algorithm 1's order, each pair once).
+// d_B receives B (device u64).  MODE_EDGE also adds b_e to be (device,
+// canonical ids, zeroed by the caller); MODE_TOTAL ignores be.
+int wedge_count(bfc_graph *g, Plan &p, Mode mode, unsigned long long *d_B, uint64_t *be, cudaStream_t s);
 // TOTAL mode on a disjoint union: also adds each start vertex's pair sum to
 // gB[grp_of_rank[rank]].
 int wedge_count_groups(bfc_graph *g, Plan &p, const uint32_t *grp_of_rank, unsigned long long *gB,

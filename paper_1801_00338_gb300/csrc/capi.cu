@@ -78,7 +78,7 @@ int bfc_graph_free(bfc_graph *g) {
     for (DBuf *b : bufs) dfree(*b, s);
   }
   DBuf *gb[] = {&g->offU, &g->nbrU, &g->offV, &g->nbrV, &g->eidV, &g->degU, &g->degV, &g->err, &g->acc, &g->scr.buf,
-                &g->beM, &g->bSr};
+                &g->beM};
   for (DBuf *b : gb) dfree(*b, s);
   cudaStreamSynchronize(s);
   delete g;
@@ -136,7 +136,7 @@ int bfc_exact(bfc_graph *g, uint32_t flags, uint64_t *out_B, int *out_side, void
   cudaStream_t s = as_stream(stream);
   int side = 0;
   BFC_TRY(prepare(g, flags, s, &side));
-  BFC_TRY(wedge_count(g, g->plan[side], MODE_TOTAL, acc_B(g), nullptr, nullptr, nullptr, s));
+  BFC_TRY(wedge_count(g, g->plan[side], MODE_TOTAL, acc_B(g), nullptr, s));
   BFC_TRY(finish_count(g, out_B, s));
   if (out_side) *out_side = side;
   return BFC_OK;
@@ -180,7 +180,7 @@ static int ordered_local(bfc_graph *g, uint32_t flags, uint64_t *bU, uint64_t *b
   }
   int rc = BFC_OK;
   if (g->m > 0 && cudaMemsetAsync(pe, 0, g->m * 8, s) != cudaSuccess) rc = BFC_ECUDA;
-  if (!rc) rc = wedge_count(g, g->plan[side], MODE_EDGE, acc_B(g), nullptr, nullptr, pe, s);
+  if (!rc) rc = wedge_count(g, g->plan[side], MODE_EDGE, acc_B(g), pe, s);
   if (!rc && bU) rc = vertex_from_edges(ptr<uint64_t>(g->offU), g->nU, nullptr, pe, bU, s);
   if (!rc && bV) rc = vertex_from_edges(ptr<uint64_t>(g->offV), g->nV, ptr<uint32_t>(g->eidV), pe, bV, s);
   if (!rc) rc = finish_count(g, out_B, s);

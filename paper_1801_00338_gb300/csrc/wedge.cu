@@ -87,11 +87,11 @@ struct WArgs {
   uint32_t list_n;
   unsigned int *queue;
   unsigned long long *B;
-  unsigned long long *bS, *bM, *be;
-  // ordered VERTEX / EDGE modes: scattered updates go to these, then one pass
-  // moves them to bS (by vertex id) and be (by canonical edge id):
-  unsigned long long *beM;  // per midpoint-row entry: lanes of a warp hit consecutive words
-  unsigned long long *bSr;  // per start rank: the hot top ranks stay in L2
+  unsigned long long *bS, *be;  // LOCAL mode: b of the start vertex (by id); LOCAL / EDGE: b_e (canonical ids)
+  // ordered EDGE mode: the far edge's updates go to beM (per midpoint-row
+  // entry, so lanes of a warp hit consecutive words); one pass then adds
+  // them to be by canonical edge id
+  unsigned long long *beM;
   uint32_t *err;
   // big class: segment scratch (per CTA, seg_cap entries each)
   uint32_t *seg;        // 5 u32 per segment: begin, end, cur, pstart, next
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(WH_WARPS * 32) k_warp_class(WArgs a) {
       if (!Full<MODE>::value || w != r) wh_insert(keys, cnts, w);
     });
     __syncwarp();
-    if (MODE == MODE_VERTEX || MODE == MODE_EDGE) {
+    if (MODE == MODE_EDGE) {
       // second sweep: every wedge learns its final multiplicity
       warp_for_each_wedge<false>(a, rb, re, [&](uint32_t i, uint64_t j) {
         uint32_t c = wh_lookup(keys, cnts, a.mR[i]);
@@ -239,7 +239,6 @@ __global__ void __launch_bounds__(WH_WARPS * 32) k_warp_class(WArgs a) {
             atomicAdd(&a.beM[i], (unsigned long long)(c - 1));
             atomicAdd(&a.be[a.sEid[j]], (unsigned long long)(c - 1));
           }
-          if (MODE == MODE_VERTEX) atomicAdd(&a.bM[a.sX[j]], (unsigned long long)(c - 1));
         }
       });
       __syncwarp();
@@ -258,7 +257,6 @@ __global__ void __launch_bounds__(WH_WARPS * 32) k_warp_class(WArgs a) {
       if (k != EMPTY_KEY) {
         uint64_t p = pairs_of(cnts[i]);
         acc += p;
-        if (MODE == MODE_VERTEX && p) atomicAdd(&a.bSr[k], (unsigned long long)p);
         keys[i] = EMPTY_KEY;
         cnts[i] = 0;
       }
@@ -266,7 +264,6 @@ __global__ void __launch_bounds__(WH_WARPS * 32) k_warp_class(WArgs a) {
     acc = warp_sum_u64(acc);
     if (lane == 0) {
       localB += acc;
-      if (MODE == MODE_VERTEX && acc) atomicAdd(&a.bSr[r], (unsigned long long)acc);
       if (MODE == MODE_SINGLE) a.bitem[item] = acc;
       if (MODE == MODE_LOCAL && a.bS) a.bS[a.vert_of[r]] = acc;
       if (MODE == MODE_TOTAL && a.gB && acc) atomicAdd(&a.gB[a.grp[r]], (unsigned long long)acc);
@@ -303,11 +300,6 @@ struct Ctr {
     uint32_t wi, sh;
     at(idx, wi, sh);
     return (atomicAdd(&c[wi], 1u << sh) >> sh) & MASK;
-  }
-  __device__ static __forceinline__ uint32_t take(uint32_t *c, uint32_t idx) {
-    uint32_t wi, sh;
-    at(idx, wi, sh);
-    return (atomicAnd(&c[wi], ~(MASK << sh)) >> sh) & MASK;
   }
   __device__ static __forceinline__ uint32_t peek(const uint32_t *c, uint32_t idx) {
     uint32_t wi, sh;
@@ -374,9 +366,8 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, P) k_cta_win(WArgs a) {
   __shared__ uint32_t wtot[32];
   constexpr int NW = WIN_THREADS / 32;
   constexpr uint32_t Z = C::Z;
-  // B accumulates at increment time except in VERTEX mode, whose exchange
-  // needs each target's final count anyway (b_w += C(c, 2))
-  constexpr bool ACC = (MODE != MODE_VERTEX);
+  // B accumulates at increment time (the sum of old values is C(c, 2))
+  constexpr bool ACC = true;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (uint32_t i = threadIdx.x; i < WIN_WORDS; i += WIN_THREADS) ctr[i] = 0;
   uint64_t localB = 0;
@@ -451,7 +442,7 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, P) k_cta_win(WArgs a) {
         }
         wcount += cur - ps;
       }
-      if ((MODE == MODE_VERTEX || MODE == MODE_EDGE || (MODE == MODE_LOCAL && a.be)) && lane == 0 && wcount)
+      if ((MODE == MODE_EDGE || (MODE == MODE_LOCAL && a.be)) && lane == 0 && wcount)
         atomicAdd(&sh_win[par], (unsigned long long)wcount);
       __syncthreads();
       // the other parity's state was last read before this barrier: reset it
@@ -463,7 +454,7 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, P) k_cta_win(WArgs a) {
       }
       const uint32_t nm = sh_min[par];
       // ---- VERTEX / EDGE: every wedge of the window reads its final count
-      if (MODE == MODE_VERTEX || MODE == MODE_EDGE || MODE == MODE_LOCAL) {
+      if (MODE == MODE_EDGE || MODE == MODE_LOCAL) {
         if (sh_win[par]) {
           while (true) {
             uint32_t s = 0;
@@ -484,36 +475,13 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, P) k_cta_win(WArgs a) {
             if (lane == 0 && rowsum) {
               const uint64_t j = rb + s_row[s];
               if (a.be) atomicAdd(&a.be[a.sEid[j]], (unsigned long long)rowsum);
-              if (MODE == MODE_VERTEX) atomicAdd(&a.bM[a.sX[j]], (unsigned long long)rowsum);
             }
           }
           __syncthreads();
         }
       }
-      // ---- clear the window (VERTEX: C(c, 2) once per distinct w as it clears)
-      if (MODE == MODE_VERTEX) {
-        if (threadIdx.x == 0) sh_q[par ^ 1] = 0;  // reused below as the exchange queue of this window
-        __syncthreads();
-        while (true) {
-          uint32_t s = 0;
-          if (lane == 0) s = atomicAdd(&sh_q[par ^ 1], 1u);
-          s = __shfl_sync(0xffffffffu, s, 0);
-          if (s >= nseg) break;
-          const uint32_t ps = s_ps[s], pe = s_cur[s];
-          for (uint32_t i = ps + lane; i < pe; i += 32) {
-            const uint32_t w = __ldg(&a.mR[i]);
-            const uint32_t c = C::take(ctr, w - lo);
-            if (c > 1) {
-              const uint64_t p = pairs_of(c);
-              acc += p;
-              atomicAdd(&a.bSr[w], (unsigned long long)p);
-            }
-          }
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) sh_q[par ^ 1] = 0;
-      } else {
-        // every target of the window has been counted: zero the words in use
+      // ---- every target of the window has been counted: zero the words in use
+      {
         const uint32_t used = (uint32_t)umin64((uint64_t)WIN_WORDS, (uint64_t)(hi - lo));
         uint4 *c4 = reinterpret_cast<uint4 *>(ctr);
         const uint32_t n4 = (used + 3) / 4;
@@ -529,7 +497,6 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, P) k_cta_win(WArgs a) {
     __syncthreads();
     if (threadIdx.x == 0) {
       localB += sh_acc;
-      if (MODE == MODE_VERTEX && sh_acc) atomicAdd(&a.bSr[r], sh_acc);
       if (MODE == MODE_SINGLE) a.bitem[item] = sh_acc;
       if (MODE == MODE_LOCAL && a.bS) a.bS[a.vert_of[r]] = sh_acc;
       if (MODE == MODE_TOTAL && a.gB && sh_acc) atomicAdd(&a.gB[a.grp[r]], sh_acc);
@@ -623,7 +590,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_big(WArgs a) {
         if (lane == 0 && nxt != INF_RANK) atomicMin(&s_next_min, nxt);
       }
       __syncthreads();
-      if (MODE == MODE_VERTEX || MODE == MODE_EDGE || (MODE == MODE_LOCAL && a.be)) {
+      if (MODE == MODE_EDGE || (MODE == MODE_LOCAL && a.be)) {
         for (uint32_t sidx = warp; sidx < nseg; sidx += NW) {
           uint32_t *sg = seg + (size_t)sidx * 5;
           uint32_t ps = sg[3], pe = sg[2];
@@ -640,7 +607,6 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_big(WArgs a) {
           rowsum = warp_sum_u64(rowsum);
           if (lane == 0 && rowsum) {
             if (a.be) atomicAdd(&a.be[a.sEid[j]], (unsigned long long)rowsum);
-            if (MODE == MODE_VERTEX) atomicAdd(&a.bM[a.sX[j]], (unsigned long long)rowsum);
           }
         }
         __syncthreads();
@@ -656,7 +622,6 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_big(WArgs a) {
           if (c > 1) {
             uint64_t p = pairs_of(c);
             acc += p;
-            if (MODE == MODE_VERTEX) atomicAdd(&a.bSr[w], (unsigned long long)p);
           }
         }
       }
@@ -673,7 +638,6 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_big(WArgs a) {
     }
     if (threadIdx.x == 0) {
       localB += s_acc;
-      if (MODE == MODE_VERTEX && s_acc) atomicAdd(&a.bSr[r], s_acc);
       if (MODE == MODE_SINGLE) a.bitem[item] = s_acc;
       if (MODE == MODE_LOCAL && a.bS) a.bS[a.vert_of[r]] = s_acc;
       if (MODE == MODE_TOTAL && a.gB && s_acc) atomicAdd(&a.gB[a.grp[r]], s_acc);
@@ -812,9 +776,9 @@ static int sm_count() {
 }
 
 static const char *tag_of(int kind, int mode) {
-  static const char *tags[3][5] = {{"warp.total", "warp.vertex", "warp.edge", "warp.single", "warp.local"},
-                                   {"win.total", "win.vertex", "win.edge", "win.single", "win.local"},
-                                   {"big.total", "big.vertex", "big.edge", "big.single", "big.local"}};
+  static const char *tags[3][4] = {{"warp.total", "warp.edge", "warp.single", "warp.local"},
+                                   {"win.total", "win.edge", "win.single", "win.local"},
+                                   {"big.total", "big.edge", "big.single", "big.local"}};
   return tags[kind][mode];
 }
 
@@ -1079,17 +1043,11 @@ int vertex_from_edges(const uint64_t *off, uint32_t n, const uint32_t *eid, cons
   return BFC_OK;
 }
 
-// move the staged sums to their outputs: be[canonical id] += beM[row entry],
-// bS[vertex id] += bSr[rank]
+// move the staged sums to their outputs: be[canonical id] += beM[row entry]
 __global__ void k_finish_edges(const uint32_t *mEid, uint64_t m, const unsigned long long *beM,
                                unsigned long long *be) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x)
     be[mEid[i]] += beM[i];  // every canonical edge appears once in midpoint-row order
-}
-__global__ void k_finish_vertices(const uint32_t *vert_of, uint32_t nS, const unsigned long long *bSr,
-                                  unsigned long long *bS) {
-  for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nS; r += (uint64_t)gridDim.x * blockDim.x)
-    bS[vert_of[r]] += bSr[r];
 }
 
 // ---------------------------------------------------------------------------
@@ -1146,37 +1104,24 @@ int wedge_count_below(bfc_graph *g, Plan &p, uint32_t rank_end, unsigned long lo
   return launch_classes<MODE_TOTAL>(g, p, a, s);
 }
 
-int wedge_count(bfc_graph *g, Plan &p, Mode mode, unsigned long long *d_B, uint64_t *bS, uint64_t *bM, uint64_t *be,
-                cudaStream_t s) {
+int wedge_count(bfc_graph *g, Plan &p, Mode mode, unsigned long long *d_B, uint64_t *be, cudaStream_t s) {
   WArgs a = args_of(g, p);
   a.B = d_B;
-  a.bS = reinterpret_cast<unsigned long long *>(bS);
-  a.bM = reinterpret_cast<unsigned long long *>(bM);
   a.be = reinterpret_cast<unsigned long long *>(be);
   if (be && p.m) {
     BFC_TRY(dalloc(g->beM, p.m * 8, s));
     BFC_CUDA_TRY(cudaMemsetAsync(g->beM.p, 0, p.m * 8, s));
     a.beM = ptr<unsigned long long>(g->beM);
   }
-  if (bS && p.nS) {
-    BFC_TRY(dalloc(g->bSr, (uint64_t)p.nS * 8, s));
-    BFC_CUDA_TRY(cudaMemsetAsync(g->bSr.p, 0, (uint64_t)p.nS * 8, s));
-    a.bSr = ptr<unsigned long long>(g->bSr);
-  }
   int rc = BFC_EINVAL;
   switch (mode) {
     case MODE_TOTAL: rc = launch_classes<MODE_TOTAL>(g, p, a, s); break;
-    case MODE_VERTEX: rc = launch_classes<MODE_VERTEX>(g, p, a, s); break;
     case MODE_EDGE: rc = launch_classes<MODE_EDGE>(g, p, a, s); break;
     default: break;
   }
   if (rc) return rc;
   if (a.beM) {
     k_finish_edges<<<grid_for(p.m, 256), 256, 0, s>>>(ptr<uint32_t>(p.mEid), p.m, a.beM, a.be);
-    BFC_LAUNCHED();
-  }
-  if (a.bSr) {
-    k_finish_vertices<<<grid_for(p.nS, 256), 256, 0, s>>>(ptr<uint32_t>(p.vert_of), p.nS, a.bSr, a.bS);
     BFC_LAUNCHED();
   }
   return BFC_OK;

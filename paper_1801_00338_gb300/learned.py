@@ -161,7 +161,7 @@ def time_vsamp(G: "bfc.Graph", k: int, trials: int, seed: int, prop=None, reps: 
 
 def evaluate(train_count: int = 200, m_lo: float = 1e4, m_hi: float = 1e6, steps: int = 2000,
              heldout=(5_000_000, 10_000_000, 100_000_000, 2.3, 2.3, 10_000), k_timing: int = 4096,
-             trials_check: int = 30, seed: int = 0) -> dict:
+             trials_check: int = 30, seed: int = 0, check_budget_s: float = 60.0) -> dict:
     """Train on generated graphs, then compare uniform and learned VSamp on a
     held-out graph: exact single-draw variances (from exact vBFC counts), the
     draws each needs for a 1% median relative error, the GPU time per draw,
@@ -210,17 +210,18 @@ def evaluate(train_count: int = 200, m_lo: float = 1e4, m_hi: float = 1e6, steps
         var_l = single_draw_variance(b, q)
         k_u = draws_for_median_error(var_u, B)
         k_l = draws_for_median_error(var_l, B)
-        t_u = time_vsamp(G, k_timing, 1, 7) / k_timing
-        t_l = time_vsamp(G, k_timing, 1, 7, prop) / k_timing
+        t_u = time_vsamp(G, k_timing, 8, 7) / (8 * k_timing)
+        t_l = time_vsamp(G, k_timing, 8, 7, prop) / (8 * k_timing)
         res = {"var_uniform": var_u, "var_learned": var_l, "var_ratio": var_l / var_u,
                "draws_1pct_uniform": k_u, "draws_1pct_learned": k_l,
                "s_per_draw_uniform": t_u, "s_per_draw_learned": t_l, "proposal_build_s": t_prop,
                "time_1pct_uniform_s": k_u * t_u, "time_1pct_learned_s": k_l * t_l + t_prop}
         res["time_ratio"] = res["time_1pct_learned_s"] / res["time_1pct_uniform_s"]
-        # empirical check at those draw counts (capped to keep the run short);
-        # these long calls also give the per-draw times used for the time to 1%
-        for name, kk, p in (("uniform", k_u, None), ("learned", k_l, prop)):
-            kk = int(min(kk, 2_000_000))
+        # empirical check at those draw counts (capped so that each check takes
+        # about `check_budget_s`); these long calls also give the per-draw
+        # times used for the time to 1%
+        for name, kk, p, t_pilot in (("uniform", k_u, None, t_u), ("learned", k_l, prop, t_l)):
+            kk = int(max(1, min(kk, check_budget_s / (trials_check * t_pilot))))
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             est = G.vsamp(kk, trials_check, 1234, proposal=p)
