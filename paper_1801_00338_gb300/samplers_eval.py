@@ -53,13 +53,14 @@ def run(g, budget_s: float = 60.0, reps: int = 1000, p_espar: float = 0.05) -> d
         b = torch.cat([lU, lV]).to(torch.float64)
         be = le.to(torch.float64)
         # exact single-draw variances
-        var = {"vsamp": float((n / 16.0) * (b * b).sum() - B * B),
-               "esamp": float((m / 16.0) * (be * be).sum() - B * B)}
+        Bf = float(B)
+        var = {"vsamp": (n / 16.0) * float((b * b).sum().item()) - Bf * Bf,
+               "esamp": (m / 16.0) * float((be * be).sum().item()) - Bf * Bf}
         cu, cv = G.edges()
         dU = torch.bincount(cu.long(), minlength=g.nU).to(torch.float64)
         dV = torch.bincount(cv.long(), minlength=g.nV).to(torch.float64)
         dd = dU[cu.long()] * dV[cv.long()]
-        var["esamp_fast"] = var["esamp"] + float((m / 16.0) * (be * dd - be * be).sum() / reps)
+        var["esamp_fast"] = var["esamp"] + (m / 16.0) * float((be * dd - be * be).sum().item()) / reps
         del lU, lV, le, b, be, cu, cv, dd
         samplers = {
             "vsamp": lambda k, T, s: G.vsamp(k, T, s),
