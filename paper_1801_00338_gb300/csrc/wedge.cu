@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, P) k_cta_win(WArgs a) {
   uint32_t *s_row = s_nx + WIN_SMAX;
   // window state, double buffered by window parity so that a window needs
   // two barriers: one after counting, one after clearing
-  __shared__ uint32_t sh_min[2], sh_q[2], sh_q2[2];
+  __shared__ uint32_t sh_min[2];
   __shared__ unsigned long long sh_win[2];
   __shared__ uint32_t sh_idx, sh_carry;
   __shared__ unsigned long long sh_acc;
@@ -377,8 +377,8 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, P) k_cta_win(WArgs a) {
       sh_idx = atomicAdd(a.queue, 1u);
       sh_carry = 0;
       sh_acc = 0;
-      sh_min[0] = INF_RANK; sh_q[0] = 0; sh_q2[0] = 0; sh_win[0] = 0;
-      sh_min[1] = INF_RANK; sh_q[1] = 0; sh_q2[1] = 0; sh_win[1] = 0;
+      sh_min[0] = INF_RANK; sh_win[0] = 0;
+      sh_min[1] = INF_RANK; sh_win[1] = 0;
     }
     __syncthreads();
     const uint32_t idx = sh_idx;
@@ -423,58 +423,70 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, P) k_cta_win(WArgs a) {
     uint32_t hi = (uint32_t)umin64((uint64_t)a.nS, (uint64_t)lo + Z);
     uint64_t acc = 0;  // per thread, over the whole vertex
     for (uint32_t par = 0;; par ^= 1) {
-      // ---- count: warps take segments from a shared queue
-      uint32_t wcount = 0;
-      while (true) {
-        uint32_t s = 0;
-        if (lane == 0) s = atomicAdd(&sh_q[par], 1u);
-        s = __shfl_sync(0xffffffffu, s, 0);
-        if (s >= nseg) break;
-        uint32_t cur = s_cur[s], nx = s_nx[s];
-        const uint32_t end = s_end[s], ps = cur;
-        if (cur < end && nx < hi) count_segment<MODE, CW, WIN_WORDS, ACC>(a.mR, cur, end, lo, hi, r, ctr, nx, acc);
-        else if (cur >= end) nx = INF_RANK;
-        if (lane == 0) {
-          s_cur[s] = cur;
-          s_ps[s] = ps;
-          s_nx[s] = nx;
-          if (nx != INF_RANK) atomicMin(&sh_min[par], nx);
+      // ---- count: warp w owns segments w, w + NW, ...; its lanes test 32 of them
+      // at once and the whole warp counts each one that has targets below hi
+      uint32_t wcount = 0, wmin = INF_RANK;
+      for (uint32_t s0 = warp; s0 < nseg; s0 += NW * 32) {
+        const uint32_t sl = s0 + (uint32_t)lane * NW;  // this lane's segment
+        uint32_t my_nx = INF_RANK;
+        bool act = false;
+        if (sl < nseg) {
+          const uint32_t c0 = s_cur[sl];
+          my_nx = (c0 < s_end[sl]) ? s_nx[sl] : INF_RANK;
+          act = my_nx < hi;  // 0: next target not loaded yet
+          s_ps[sl] = c0;     // nothing of it counted in this window yet
         }
-        wcount += cur - ps;
+        uint32_t bal = __ballot_sync(0xffffffffu, act);
+        while (bal) {
+          const int l = __ffs(bal) - 1;
+          bal &= bal - 1;
+          const uint32_t sg = s0 + (uint32_t)l * NW;
+          uint32_t cur = s_cur[sg], nx = INF_RANK;
+          const uint32_t ps = cur;
+          count_segment<MODE, CW, WIN_WORDS, ACC>(a.mR, cur, s_end[sg], lo, hi, r, ctr, nx, acc);
+          if (lane == 0) {
+            s_cur[sg] = cur;
+            s_nx[sg] = nx;
+          }
+          if (lane == l) my_nx = nx;
+          wcount += cur - ps;
+        }
+        wmin = min(wmin, my_nx);
       }
+      for (int o = 16; o > 0; o >>= 1) wmin = min(wmin, __shfl_xor_sync(0xffffffffu, wmin, o));
+      if (lane == 0 && wmin != INF_RANK) atomicMin(&sh_min[par], wmin);
       if ((MODE == MODE_EDGE || (MODE == MODE_LOCAL && a.be)) && lane == 0 && wcount)
         atomicAdd(&sh_win[par], (unsigned long long)wcount);
       __syncthreads();
       // the other parity's state was last read before this barrier: reset it
       if (threadIdx.x == 0) {
         sh_min[par ^ 1] = INF_RANK;
-        sh_q[par ^ 1] = 0;
-        sh_q2[par ^ 1] = 0;
         sh_win[par ^ 1] = 0;
       }
       const uint32_t nm = sh_min[par];
-      // ---- VERTEX / EDGE: every wedge of the window reads its final count
+      // ---- EDGE / LOCAL: every wedge of the window reads its final count
       if (MODE == MODE_EDGE || MODE == MODE_LOCAL) {
         if (sh_win[par]) {
-          while (true) {
-            uint32_t s = 0;
-            if (lane == 0) s = atomicAdd(&sh_q2[par], 1u);
-            s = __shfl_sync(0xffffffffu, s, 0);
-            if (s >= nseg) break;
-            const uint32_t ps = s_ps[s], pe = s_cur[s];
-            if (ps >= pe) continue;
-            uint64_t rowsum = 0;
-            for (uint32_t i = ps + lane; i < pe; i += 32) {
-              const uint32_t c = C::peek(ctr, __ldg(&a.mR[i]) - lo);
-              if (c > 1) {
-                rowsum += c - 1;
-                if (MODE != MODE_LOCAL && a.be) atomicAdd(&a.beM[i], (unsigned long long)(c - 1));
+          // the same ownership: each warp reads back the pieces it counted
+          for (uint32_t s0 = warp; s0 < nseg; s0 += NW * 32) {
+            const uint32_t sl = s0 + (uint32_t)lane * NW;
+            const bool act = sl < nseg && s_ps[sl] < s_cur[sl];
+            uint32_t bal = __ballot_sync(0xffffffffu, act);
+            while (bal) {
+              const int l = __ffs(bal) - 1;
+              bal &= bal - 1;
+              const uint32_t sg = s0 + (uint32_t)l * NW;
+              const uint32_t ps = s_ps[sg], pe = s_cur[sg];
+              uint64_t rowsum = 0;
+              for (uint32_t i = ps + lane; i < pe; i += 32) {
+                const uint32_t c = C::peek(ctr, __ldg(&a.mR[i]) - lo);
+                if (c > 1) {
+                  rowsum += c - 1;
+                  if (MODE != MODE_LOCAL) atomicAdd(&a.beM[i], (unsigned long long)(c - 1));
+                }
               }
-            }
-            rowsum = warp_sum_u64(rowsum);
-            if (lane == 0 && rowsum) {
-              const uint64_t j = rb + s_row[s];
-              if (a.be) atomicAdd(&a.be[a.sEid[j]], (unsigned long long)rowsum);
+              rowsum = warp_sum_u64(rowsum);
+              if (lane == 0 && rowsum) atomicAdd(&a.be[a.sEid[rb + s_row[sg]]], (unsigned long long)rowsum);
             }
           }
           __syncthreads();
