@@ -584,62 +584,67 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_big(WArgs a) {
     const uint32_t nseg = min(s_carry, a.seg_cap);
     uint32_t lo = Full<MODE>::value ? 0u : r + 1;
     uint32_t hi = (uint32_t)umin64((uint64_t)a.nS, (uint64_t)lo + BIG_Z);
+    uint64_t acc = 0;  // per thread: sum of old counter values = sum C(c, 2)
     while (true) {
-      for (uint32_t sidx = warp; sidx < nseg; sidx += NW) {
-        uint32_t *sg = seg + (size_t)sidx * 5;
-        uint32_t pos = sg[2], end = sg[1], nxt = sg[4];
-        uint32_t pstart = pos;
-        if (pos < end && nxt < hi) {
-          {
-            uint64_t unused = 0;
-            count_segment<MODE, 32, BIG_Z, false>(a.mR, pos, end, lo, hi, r, ctr, nxt, unused);
-          }
-          if (lane == 0) { sg[2] = pos; sg[3] = pstart; sg[4] = nxt; }
-        } else {
-          if (lane == 0) sg[3] = pos;
-          if (pos >= end) nxt = INF_RANK;
+      // ---- count: warp w owns segments w, w + NW, ...; 32 tested per ballot
+      uint32_t wmin = INF_RANK;
+      for (uint32_t s0 = warp; s0 < nseg; s0 += NW * 32) {
+        const uint32_t sl = s0 + (uint32_t)lane * NW;
+        uint32_t my_nx = INF_RANK;
+        bool act = false;
+        if (sl < nseg) {
+          uint32_t *sg = seg + (size_t)sl * 5;
+          const uint32_t pos = sg[2];
+          my_nx = (pos < sg[1]) ? sg[4] : INF_RANK;
+          act = my_nx < hi;  // 0: next target not loaded yet
+          sg[3] = pos;       // nothing of it counted in this window yet
         }
-        if (lane == 0 && nxt != INF_RANK) atomicMin(&s_next_min, nxt);
+        uint32_t bal = __ballot_sync(0xffffffffu, act);
+        while (bal) {
+          const int l = __ffs(bal) - 1;
+          bal &= bal - 1;
+          uint32_t *sg = seg + (size_t)(s0 + (uint32_t)l * NW) * 5;
+          uint32_t pos = sg[2], nxt = INF_RANK;
+          count_segment<MODE, 32, BIG_Z, true>(a.mR, pos, sg[1], lo, hi, r, ctr, nxt, acc);
+          if (lane == 0) { sg[2] = pos; sg[4] = nxt; }
+          if (lane == l) my_nx = nxt;
+        }
+        wmin = min(wmin, my_nx);
       }
+      for (int o = 16; o > 0; o >>= 1) wmin = min(wmin, __shfl_xor_sync(0xffffffffu, wmin, o));
+      if (lane == 0 && wmin != INF_RANK) atomicMin(&s_next_min, wmin);
       __syncthreads();
       if (MODE == MODE_EDGE || (MODE == MODE_LOCAL && a.be)) {
-        for (uint32_t sidx = warp; sidx < nseg; sidx += NW) {
-          uint32_t *sg = seg + (size_t)sidx * 5;
-          uint32_t ps = sg[3], pe = sg[2];
-          if (ps >= pe) continue;
-          uint32_t j = seg_row[sidx];
-          uint64_t rowsum = 0;
-          for (uint32_t i = ps + lane; i < pe; i += 32) {
-            uint32_t c = ctr[a.mR[i] - lo];
-            if (c > 1) {
-              rowsum += c - 1;
-              if (MODE != MODE_LOCAL && a.be) atomicAdd(&a.beM[i], (unsigned long long)(c - 1));
+        for (uint32_t s0 = warp; s0 < nseg; s0 += NW * 32) {
+          const uint32_t sl = s0 + (uint32_t)lane * NW;
+          const bool act = sl < nseg && seg[(size_t)sl * 5 + 3] < seg[(size_t)sl * 5 + 2];
+          uint32_t bal = __ballot_sync(0xffffffffu, act);
+          while (bal) {
+            const int l = __ffs(bal) - 1;
+            bal &= bal - 1;
+            const uint32_t sidx = s0 + (uint32_t)l * NW;
+            const uint32_t *sg = seg + (size_t)sidx * 5;
+            const uint32_t ps = sg[3], pe = sg[2];
+            uint64_t rowsum = 0;
+            for (uint32_t i = ps + lane; i < pe; i += 32) {
+              const uint32_t c = ctr[__ldg(&a.mR[i]) - lo];
+              if (c > 1) {
+                rowsum += c - 1;
+                if (MODE != MODE_LOCAL) atomicAdd(&a.beM[i], (unsigned long long)(c - 1));
+              }
             }
-          }
-          rowsum = warp_sum_u64(rowsum);
-          if (lane == 0 && rowsum) {
-            if (a.be) atomicAdd(&a.be[a.sEid[j]], (unsigned long long)rowsum);
+            rowsum = warp_sum_u64(rowsum);
+            if (lane == 0 && rowsum) atomicAdd(&a.be[a.sEid[seg_row[sidx]]], (unsigned long long)rowsum);
           }
         }
         __syncthreads();
       }
-      uint64_t acc = 0;
-      for (uint32_t sidx = warp; sidx < nseg; sidx += NW) {
-        uint32_t *sg = seg + (size_t)sidx * 5;
-        uint32_t ps = sg[3], pe = sg[2];
-        for (uint32_t i = ps + lane; i < pe; i += 32) {
-          uint32_t w = a.mR[i];
-          if (Full<MODE>::value && w == r) continue;
-          uint32_t c = atomicExch(&ctr[w - lo], 0u);
-          if (c > 1) {
-            uint64_t p = pairs_of(c);
-            acc += p;
-          }
-        }
+      // ---- every target of the window has been counted: zero the words in use
+      {
+        const uint32_t used = (uint32_t)umin64((uint64_t)BIG_Z, (uint64_t)(hi - lo));
+        uint4 *c4 = reinterpret_cast<uint4 *>(ctr);
+        for (uint32_t i = threadIdx.x; i < (used + 3) / 4; i += CT_THREADS) c4[i] = make_uint4(0, 0, 0, 0);
       }
-      acc = warp_sum_u64(acc);
-      if (lane == 0 && acc) atomicAdd(&s_acc, (unsigned long long)acc);
-      __syncthreads();
       const uint32_t nm = s_next_min;
       __syncthreads();
       if (nm == INF_RANK) break;
@@ -648,6 +653,9 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_big(WArgs a) {
       hi = (uint32_t)umin64((uint64_t)a.nS, (uint64_t)lo + BIG_Z);
       __syncthreads();
     }
+    acc = warp_sum_u64(acc);
+    if (lane == 0 && acc) atomicAdd(&s_acc, (unsigned long long)acc);
+    __syncthreads();
     if (threadIdx.x == 0) {
       localB += s_acc;
       if (MODE == MODE_SINGLE) a.bitem[item] = s_acc;
