@@ -37,6 +37,23 @@ CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.a
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
 
+# DRAM bytes (read + write) per call of each counting-kernel set, from one ncu
+# capture of this workload (profiles/win_edge_chung_lu_1m_5m.md), valid only
+# for the kernel source they were taken with (its SHA-256 prefix).
+MEASURED_TRAFFIC = {"source_sha256": "7d7305d7323b8293",
+                    "bytes": {"win.edge": 17.01e9, "win.total": 5.69e9, "big.edge": 7.36e9}}
+
+
+def measured_traffic(tag: str):
+    import hashlib
+    src = os.path.join(ROOT, "paper_1801_00338_gb300", "csrc", "wedge.cu")
+    with open(src, "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()[:16]
+    if h != MEASURED_TRAFFIC["source_sha256"]:
+        return None
+    return MEASURED_TRAFFIC["bytes"].get(tag)
+
+
 def measured_peaks(key: str = "hbm_gbs"):
     """(peak, 'measured' | 'fallback') for hbm_gbs (GB/s) or a bf16 TFLOP/s key."""
     fallback = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
@@ -303,7 +320,7 @@ def run_own(args, rank, world, local_rank):
     avg_ms = tot_ms / max(n_launch, 1)
     achieved = alg_bytes / (avg_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": {"warp": "k_warp_class", "win": "k_cta_win", "big": "k_cta_big"}[cls] + f"<{mode}>", "peak_kind": peak_kind,
+                "traffic": measured_traffic(dom), "kernel": {"warp": "k_warp_class", "win": "k_cta_win", "big": "k_cta_big"}[cls] + f"<{mode}>", "peak_kind": peak_kind,
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms}
 
     # the hub block's tile kernel: upper-triangle 128 x 128 tiles over K padded to 64

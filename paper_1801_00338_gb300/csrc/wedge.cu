@@ -706,10 +706,13 @@ __global__ void k_scatter_class(const uint32_t *cls_of, uint32_t nS, const unsig
     list[begin[c] + p] = (uint32_t)r;
   }
 }
-__global__ void k_work_keys(const uint32_t *list, uint32_t n, const uint64_t *work, uint64_t *keys, uint32_t *vals) {
+// 16-bit sort key for "heaviest first": the work's float exponent and top 7
+// mantissa bits (order within 1%), complemented so that an ascending sort
+// puts the largest work first
+__global__ void k_work_keys(const uint32_t *list, uint32_t n, const uint64_t *work, uint32_t *keys, uint32_t *vals) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t r = list[i];
-    keys[i] = ~work[r];  // ascending sort of ~work = descending work
+    const uint32_t r = list[i];
+    keys[i] = 0xFFFFu - (__float_as_uint((float)work[r]) >> 16);
     vals[i] = r;
   }
 }
@@ -762,16 +765,16 @@ int plan_classify(bfc_graph *g, Plan &p, cudaStream_t s) {
   uint32_t maxn = 0;
   for (int c = CLS_S0; c < N; c++) maxn = std::max(maxn, p.cls_count[c]);
   if (maxn > 1) {
-    PC_TRY(dalloc(k1, (uint64_t)maxn * 8, s));
-    PC_TRY(dalloc(k2, (uint64_t)maxn * 8, s));
+    PC_TRY(dalloc(k1, (uint64_t)maxn * 4, s));
+    PC_TRY(dalloc(k2, (uint64_t)maxn * 4, s));
     PC_TRY(dalloc(v2, (uint64_t)maxn * 4, s));
     for (int c = CLS_S0; c < N; c++) {
       const uint32_t nc = p.cls_count[c];
       if (nc < 2) continue;
       uint32_t *list = ptr<uint32_t>(p.cls) + p.cls_begin[c];
-      k_work_keys<<<grid_for(nc, 256), 256, 0, s>>>(list, nc, ptr<uint64_t>(p.work), ptr<uint64_t>(k1), list);
+      k_work_keys<<<grid_for(nc, 256), 256, 0, s>>>(list, nc, ptr<uint64_t>(p.work), ptr<uint32_t>(k1), list);
       count_launch();
-      PC_TRY(radix_sort_u64(ptr<uint64_t>(k1), ptr<uint64_t>(k2), list, ptr<uint32_t>(v2), nc, 64, g->scr, s));
+      PC_TRY(radix_sort_u32(ptr<uint32_t>(k1), ptr<uint32_t>(k2), list, ptr<uint32_t>(v2), nc, 16, g->scr, s));
       BFC_CUDA_TRY(cudaMemcpyAsync(list, v2.p, (uint64_t)nc * 4, cudaMemcpyDeviceToDevice, s));
     }
   }
