@@ -262,6 +262,30 @@ int bfc_esamp(bfc_graph *g, uint64_t k, uint32_t reps, uint32_t trials, uint64_t
 int bfc_wsamp(bfc_graph *g, uint64_t k, uint32_t trials, uint64_t seed, double *est, uint64_t *centres,
               uint64_t *betas, void *stream);
 
+/* ---- (epsilon, delta) amplification of the sampling estimators ------------ */
+
+/* Median of means (Section 5.1: averages of independent instances, made an
+ * (epsilon, delta) estimator by the median of O(log 1/delta) of them).
+ *   y      (host, n values): estimator instances, e.g. single-draw terms or
+ *          per-trial estimates; split into `groups` consecutive groups of
+ *          n / groups values (n must be a positive multiple of groups).
+ *   out    (host): the median of the group means (the mean of the two middle
+ *          ones when groups is even).
+ * Errors: BFC_EINVAL (null pointers, groups == 0, n % groups != 0, n == 0). */
+int bfc_median_of_means(const double *y, uint64_t n, uint32_t groups, double *out);
+
+/* Sizes for an (epsilon, delta) estimate from the variance var1 of one
+ * instance and the count B (or estimates of both):
+ *   alpha  = ceil(32 var1 / (epsilon^2 B^2)) instances per group, so that by
+ *            Chebyshev a group mean misses B by epsilon B with probability
+ *            <= 1/32 (the choice of alpha in Section 5.1);
+ *   groups = ceil(ln(1/delta) / (2 (1/2 - 1/32)^2)), odd, so that by
+ *            Hoeffding's inequality at least half of the groups miss with
+ *            probability <= delta.
+ * Errors: BFC_EINVAL (var1 < 0, B <= 0, epsilon <= 0, delta not in (0, 1),
+ * null outputs), BFC_ERANGE (alpha beyond 2^63). */
+int bfc_mom_sizes(double var1, double B, double epsilon, double delta, uint64_t *alpha, uint32_t *groups);
+
 /* A sampling proposal from integer weights (device or host per flags
  * BFC_INPUT_DEVICE), one per population index (nU + nV entries, U first).
  * The weights are copied; W = sum must be > 0. */

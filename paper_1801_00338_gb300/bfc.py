@@ -64,6 +64,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "bfc_vsamp": [P, u64, P, u32, u64, P, P, P, P],
         "bfc_esamp": [P, u64, u32, u32, u64, P, P, P, P],
         "bfc_wsamp": [P, u64, u32, u64, P, P, P, P],
+        "bfc_median_of_means": [P, u64, u32, P],
+        "bfc_mom_sizes": [dbl, dbl, dbl, dbl, P, P],
         "bfc_proposal_from_weights": [P, P, u32, P, P],
         "bfc_proposal_free": [P],
         "bfc_exact_csr_noalloc": [P, P, u32, P, P, u32, u32, P, P],
@@ -341,6 +343,22 @@ def bfc_wsamp(h: int, k: int, trials: int, seed: int, want_draws: bool = False, 
     if want_draws:
         return est, cd[: trials * k], bd[: trials * k]
     return est
+
+
+def bfc_median_of_means(y, groups: int) -> float:
+    """Median of the means of `groups` consecutive groups of the values y."""
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    out = ctypes.c_double()
+    _check(load().bfc_median_of_means(y.ctypes.data, y.size, groups, ctypes.byref(out)), "bfc_median_of_means")
+    return float(out.value)
+
+
+def bfc_mom_sizes(var1: float, B: float, epsilon: float, delta: float) -> tuple[int, int]:
+    """(instances per group, groups) of an (epsilon, delta) median-of-means estimate."""
+    a = ctypes.c_uint64()
+    g = ctypes.c_uint32()
+    _check(load().bfc_mom_sizes(var1, B, epsilon, delta, ctypes.byref(a), ctypes.byref(g)), "bfc_mom_sizes")
+    return int(a.value), int(g.value)
 
 
 MLP_FEATURES = 6

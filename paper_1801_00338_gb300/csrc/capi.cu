@@ -1,5 +1,7 @@
 // C ABI entry points (declared in include/bfc.h).
 #include <algorithm>
+#include <cmath>
+#include <vector>
 #include <new>
 
 #include "bfc_internal.cuh"
@@ -229,6 +231,34 @@ int bfc_plan_stats(bfc_graph *g, int side, uint64_t *out, void *stream) {
     out[1 + 2 * Plan::NCLS + c] = p.cls_rows[c];
   }
   out[1 + 3 * Plan::NCLS] = p.total_work;
+  return BFC_OK;
+}
+
+int bfc_median_of_means(const double *y, uint64_t n, uint32_t groups, double *out) {
+  if (!y || !out || groups == 0 || n == 0 || n % groups) return BFC_EINVAL;
+  const uint64_t per = n / groups;
+  std::vector<double> mean(groups);
+  for (uint32_t gi = 0; gi < groups; gi++) {
+    double sum = 0.0;
+    for (uint64_t i = 0; i < per; i++) sum += y[(uint64_t)gi * per + i];
+    mean[gi] = sum / (double)per;
+  }
+  std::sort(mean.begin(), mean.end());
+  *out = (groups & 1) ? mean[groups / 2] : 0.5 * (mean[groups / 2 - 1] + mean[groups / 2]);
+  return BFC_OK;
+}
+
+int bfc_mom_sizes(double var1, double B, double epsilon, double delta, uint64_t *alpha, uint32_t *groups) {
+  if (!alpha || !groups || !(var1 >= 0.0) || !(B > 0.0) || !(epsilon > 0.0) || !(delta > 0.0 && delta < 1.0))
+    return BFC_EINVAL;
+  const double a = std::ceil(32.0 * var1 / (epsilon * epsilon * B * B));
+  if (!(a < 9.2e18)) return BFC_ERANGE;
+  const double margin = 0.5 - 1.0 / 32.0;
+  uint32_t g = (uint32_t)std::ceil(std::log(1.0 / delta) / (2.0 * margin * margin));
+  if (g == 0) g = 1;
+  if (!(g & 1)) g++;
+  *alpha = a < 1.0 ? 1 : (uint64_t)a;
+  *groups = g;
   return BFC_OK;
 }
 

@@ -120,3 +120,21 @@ def test_edge_cases(bfc):
         est, cd, bd = G.wsamp(40, 2, 3, want_draws=True)
         cd, bd = u64(cd), u64(bd)
         assert np.array_equal(bd, np.where(cd < 5, 4, 3))
+
+
+def test_median_of_means_estimates_meet_epsilon(bfc):
+    """(epsilon, delta) estimates (pilot-sized alpha and groups, median of
+    group means) from each sampler land within epsilon B of the oracle's B in
+    at least 1 - delta of the seeds (the sizes leave a wide margin)."""
+    from paper_1801_00338_gb300 import mom
+    g = synth.chung_lu_scaled(3000, 9000, 60_000, 2.1, 2.4, 5)
+    B, _ = O.exact(g.u, g.v, g.nU, g.nV)
+    eps, delta, runs = 0.1, 0.2, 10
+    with bfc.Graph(g.u, g.v, g.nU, g.nV) as G:
+        for method in ("vsamp", "esamp", "esamp_fast", "wsamp", "espar"):
+            miss = 0
+            for seed in range(runs):
+                r = mom.estimate(G, method, eps, delta, seed=100 * seed, reps=64, p=0.3)
+                assert r["groups"] % 2 == 1 and r["alpha"] >= 1
+                miss += abs(r["estimate"] - B) > eps * B
+            assert miss <= delta * runs, (method, miss)
