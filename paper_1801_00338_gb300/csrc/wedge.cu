@@ -56,16 +56,29 @@ constexpr int CW_OF[5] = {2, 4, 8, 16, 32};
 constexpr int WH_WARPS = 8;
 constexpr int WH_SLOTS = 1024;                    // per warp
 constexpr uint64_t WH_MAX_WORK = WH_SLOTS / 2;    // load factor <= 1/2
-// window kernels come in two sizes: P CTAs of 1024/P threads per SM, each
-// with 49,152/P counter words and room for 1,536/P wedge-list segments.
-// Small (P = 4) keeps four vertices in flight per SM to hide the latency of
-// the dependent loads every window starts with; large (P = 1) takes the
-// vertices whose wedge lists need more segments.
+// window kernels come in two sizes (tag P_SMALL / P_LARGE).  Small: three
+// 512-thread CTAs per SM (48 warps: the dependent row loads every window
+// starts with need many warps in flight), each with 16,384 counter words and
+// room for 512 wedge-list segments; measured faster than four 256-thread CTAs
+// with 12,288 words, four 384-thread ones, or two 512-thread ones with twice
+// the window.  Large: one 1,024-thread CTA per SM with 49,152 words and 1,536
+// segments, for the vertices whose wedge lists need more segments.
 template <int P>
-struct WinCfg {
-  static constexpr int THREADS = 1024 / P;
-  static constexpr uint32_t WORDS = 48 * 1024 / P;
-  static constexpr uint32_t SMAX = 1536 / P;
+struct WinCfg;
+template <>
+struct WinCfg<4> {  // small: 3 CTAs of 16 warps per SM, 64 KB windows
+  static constexpr int THREADS = 512;
+  static constexpr int MINB = 3;
+  static constexpr uint32_t WORDS = 16 * 1024;
+  static constexpr uint32_t SMAX = 512;
+  static constexpr size_t SMEM = (size_t)WORDS * 4 + (size_t)SMAX * 5 * 4;
+};
+template <>
+struct WinCfg<1> {  // large: one CTA of 32 warps per SM, 192 KB windows
+  static constexpr int THREADS = 1024;
+  static constexpr int MINB = 1;
+  static constexpr uint32_t WORDS = 48 * 1024;
+  static constexpr uint32_t SMAX = 1536;
   static constexpr size_t SMEM = (size_t)WORDS * 4 + (size_t)SMAX * 5 * 4;
 };
 constexpr int P_SMALL = 4, P_LARGE = 1;
@@ -347,7 +360,7 @@ __device__ __forceinline__ void count_segment(const uint32_t *__restrict__ mR, u
 }
 
 template <int MODE, int CW, int P>
-__global__ void __launch_bounds__(WinCfg<P>::THREADS, P) k_cta_win(WArgs a) {
+__global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win(WArgs a) {
   constexpr int WIN_THREADS = WinCfg<P>::THREADS;
   constexpr uint32_t WIN_WORDS = WinCfg<P>::WORDS;
   constexpr uint32_t WIN_SMAX = WinCfg<P>::SMAX;
@@ -867,7 +880,7 @@ static int launch_lists(bfc_graph *g, WArgs a, const uint32_t *const *lists, con
            : cw == 8 ? k_cta_win<MODE, 8, P_LARGE> : cw == 16 ? k_cta_win<MODE, 16, P_LARGE>
                                                               : k_cta_win<MODE, 32, P_LARGE>;
     }
-    const int per_sm = small ? P_SMALL : P_LARGE;
+    const int per_sm = small ? WinCfg<P_SMALL>::MINB : WinCfg<P_LARGE>::MINB;
     const int threads = small ? WinCfg<P_SMALL>::THREADS : WinCfg<P_LARGE>::THREADS;
     const size_t smem = small ? WinCfg<P_SMALL>::SMEM : WinCfg<P_LARGE>::SMEM;
     BFC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
