@@ -160,11 +160,8 @@ int read_device_error(bfc_graph *g, cudaStream_t s);  // maps DERR_* bits to a s
 enum Mode { MODE_TOTAL = 0, MODE_EDGE = 1, MODE_SINGLE = 2, MODE_LOCAL = 3 };
 // Counts with the start side of plan p (Algorithm 1's order, each pair once).
 // d_B receives B (device u64).  MODE_EDGE also adds b_e to be (device,
-// canonical ids, zeroed by the caller) and, when bM is not null, writes the
-// midpoint side's b_x = 1/2 sum of its edges' b_e (device, by vertex id);
-// MODE_TOTAL ignores be and bM.
-int wedge_count(bfc_graph *g, Plan &p, Mode mode, unsigned long long *d_B, uint64_t *be, uint64_t *bM,
-                cudaStream_t s);
+// canonical ids, zeroed by the caller); MODE_TOTAL ignores be.
+int wedge_count(bfc_graph *g, Plan &p, Mode mode, unsigned long long *d_B, uint64_t *be, cudaStream_t s);
 // TOTAL mode on a disjoint union: also adds each start vertex's pair sum to
 // gB[grp_of_rank[rank]].
 int wedge_count_groups(bfc_graph *g, Plan &p, const uint32_t *grp_of_rank, unsigned long long *gB,

@@ -138,7 +138,7 @@ int bfc_exact(bfc_graph *g, uint32_t flags, uint64_t *out_B, int *out_side, void
   cudaStream_t s = as_stream(stream);
   int side = 0;
   BFC_TRY(prepare(g, flags, s, &side));
-  BFC_TRY(wedge_count(g, g->plan[side], MODE_TOTAL, acc_B(g), nullptr, nullptr, s));
+  BFC_TRY(wedge_count(g, g->plan[side], MODE_TOTAL, acc_B(g), nullptr, s));
   BFC_TRY(finish_count(g, out_B, s));
   if (out_side) *out_side = side;
   return BFC_OK;
@@ -182,13 +182,9 @@ static int ordered_local(bfc_graph *g, uint32_t flags, uint64_t *bU, uint64_t *b
   }
   int rc = BFC_OK;
   if (g->m > 0 && cudaMemsetAsync(pe, 0, g->m * 8, s) != cudaSuccess) rc = BFC_ECUDA;
-  // the midpoint side's counts come out of the pass that finishes b_e
-  uint64_t *bS = side ? bV : bU, *bM = side ? bU : bV;
-  if (!rc) rc = wedge_count(g, g->plan[side], MODE_EDGE, acc_B(g), pe, bM, s);
-  if (!rc && bS) {
-    if (side == 0) rc = vertex_from_edges(ptr<uint64_t>(g->offU), g->nU, nullptr, pe, bS, s);
-    else rc = vertex_from_edges(ptr<uint64_t>(g->offV), g->nV, ptr<uint32_t>(g->eidV), pe, bS, s);
-  }
+  if (!rc) rc = wedge_count(g, g->plan[side], MODE_EDGE, acc_B(g), pe, s);
+  if (!rc && bU) rc = vertex_from_edges(ptr<uint64_t>(g->offU), g->nU, nullptr, pe, bU, s);
+  if (!rc && bV) rc = vertex_from_edges(ptr<uint64_t>(g->offV), g->nV, ptr<uint32_t>(g->eidV), pe, bV, s);
   if (!rc) rc = finish_count(g, out_B, s);
   dfree(tmpE, s);
   return rc;

@@ -1086,25 +1086,6 @@ int vertex_from_edges(const uint64_t *off, uint32_t n, const uint32_t *eid, cons
 }
 
 // move the staged sums to their outputs: be[canonical id] += beM[row entry]
-// the same per midpoint row (one warp each), also writing the row's vertex
-// count b_x = 1/2 sum of its edges' final b_e
-__global__ void k_finish_edges_rows(const uint64_t *offM, uint32_t nM, const uint32_t *mEid,
-                                    const unsigned long long *beM, unsigned long long *be, unsigned long long *bM) {
-  const int lane = threadIdx.x & 31;
-  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t x = warp; x < nM; x += nw) {
-    uint64_t t = 0;
-    for (uint64_t i = offM[x] + lane; i < offM[x + 1]; i += 32) {
-      const uint32_t e = mEid[i];
-      const unsigned long long f = be[e] + beM[i];
-      be[e] = f;
-      t += f;
-    }
-    t = warp_sum_u64(t);
-    if (lane == 0) bM[x] = t / 2;
-  }
-}
 __global__ void k_finish_edges(const uint32_t *mEid, uint64_t m, const unsigned long long *beM,
                                unsigned long long *be) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x)
@@ -1165,8 +1146,7 @@ int wedge_count_below(bfc_graph *g, Plan &p, uint32_t rank_end, unsigned long lo
   return launch_classes<MODE_TOTAL>(g, p, a, s);
 }
 
-int wedge_count(bfc_graph *g, Plan &p, Mode mode, unsigned long long *d_B, uint64_t *be, uint64_t *bM,
-                cudaStream_t s) {
+int wedge_count(bfc_graph *g, Plan &p, Mode mode, unsigned long long *d_B, uint64_t *be, cudaStream_t s) {
   WArgs a = args_of(g, p);
   a.B = d_B;
   a.be = reinterpret_cast<unsigned long long *>(be);
@@ -1182,15 +1162,9 @@ int wedge_count(bfc_graph *g, Plan &p, Mode mode, unsigned long long *d_B, uint6
     default: break;
   }
   if (rc) return rc;
-  if (a.beM && bM) {
-    k_finish_edges_rows<<<grid_for((uint64_t)p.nM * 32, 256), 256, 0, s>>>(
-        p.offM, p.nM, ptr<uint32_t>(p.mEid), a.beM, a.be, reinterpret_cast<unsigned long long *>(bM));
-    BFC_LAUNCHED();
-  } else if (a.beM) {
+  if (a.beM) {
     k_finish_edges<<<grid_for(p.m, 256), 256, 0, s>>>(ptr<uint32_t>(p.mEid), p.m, a.beM, a.be);
     BFC_LAUNCHED();
-  } else if (bM && p.nM) {
-    BFC_CUDA_TRY(cudaMemsetAsync(bM, 0, (uint64_t)p.nM * 8, s));  // no edges: every count is 0
   }
   return BFC_OK;
 }
