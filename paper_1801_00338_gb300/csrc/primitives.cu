@@ -252,22 +252,31 @@ __global__ void k_rs_hist(const K *keys, uint64_t n, int shift, uint32_t *hist, 
   hist[(uint64_t)threadIdx.x * nb + blockIdx.x] = cnt[threadIdx.x];
 }
 
+// Scatter one tile: rank every element within its digit (warp match + per-warp
+// digit counters), stage the tile in shared memory in digit order, then write
+// each digit's run to its global position with consecutive threads writing
+// consecutive addresses.
 template <class K>
 __global__ void k_rs_scatter(const K *keys, const uint32_t *vals, K *kout, uint32_t *vout, uint64_t n, int shift,
                              const uint64_t *offs, uint32_t nb) {
   __shared__ uint32_t wcnt[RS_WARPS][256];
   __shared__ uint64_t gbase[256];
+  __shared__ uint32_t lstart[256];     // start of each digit's run in the staged tile
+  __shared__ uint32_t wsum[RS_WARPS];
+  __shared__ K sk[RS_TILE];
+  __shared__ uint32_t sv[RS_TILE];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
   __syncthreads();
-  uint64_t base = (uint64_t)blockIdx.x * RS_TILE + (uint64_t)warp * (32 * RS_ITEMS);
+  const uint64_t tile0 = (uint64_t)blockIdx.x * RS_TILE;
+  const uint64_t base = tile0 + (uint64_t)warp * (32 * RS_ITEMS);
   K k[RS_ITEMS];
   uint32_t v[RS_ITEMS];
   uint32_t d[RS_ITEMS];
 #pragma unroll
   for (int j = 0; j < RS_ITEMS; j++) {
-    uint64_t idx = base + (uint64_t)j * 32 + lane;
-    bool ok = idx < n;
+    const uint64_t idx = base + (uint64_t)j * 32 + lane;
+    const bool ok = idx < n;
     k[j] = ok ? keys[idx] : (K)0;
     v[j] = (ok && vals) ? vals[idx] : 0u;
     d[j] = ok ? ((uint32_t)(k[j] >> shift) & 255u) : 256u;
@@ -275,31 +284,53 @@ __global__ void k_rs_scatter(const K *keys, const uint32_t *vals, K *kout, uint3
   }
   __syncthreads();
   {
-    uint32_t t = threadIdx.x;  // one digit per thread (256 threads)
+    // thread t owns digit t: per-warp offsets within the digit, then the
+    // digit's start in the tile (exclusive scan over digits)
+    const uint32_t t = threadIdx.x;
     uint32_t run = 0;
 #pragma unroll
     for (int w = 0; w < RS_WARPS; w++) {
-      uint32_t c = wcnt[w][t];
+      const uint32_t c = wcnt[w][t];
       wcnt[w][t] = run;
       run += c;
     }
     gbase[t] = offs[(uint64_t)t * nb + blockIdx.x];
+    uint32_t incl = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    uint32_t before = 0;
+    for (int w = 0; w < warp; w++) before += wsum[w];
+    lstart[t] = before + incl - run;
   }
   __syncthreads();
   const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
   for (int j = 0; j < RS_ITEMS; j++) {
-    uint32_t peers = __match_any_sync(0xffffffffu, d[j]);
-    uint32_t rank = __popc(peers & lt);
-    uint64_t pos = 0;
-    if (d[j] < 256u) pos = gbase[d[j]] + wcnt[warp][d[j]] + rank;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d[j]);
+    const uint32_t rank = __popc(peers & lt);
+    uint32_t lp = 0;
+    if (d[j] < 256u) lp = lstart[d[j]] + wcnt[warp][d[j]] + rank;
     __syncwarp();
     if (d[j] < 256u && rank == 0) wcnt[warp][d[j]] += __popc(peers);
     __syncwarp();
     if (d[j] < 256u) {
-      kout[pos] = k[j];
-      if (vout) vout[pos] = v[j];
+      sk[lp] = k[j];
+      sv[lp] = v[j];
     }
+  }
+  __syncthreads();
+  const uint32_t cnt = (uint32_t)((n - tile0) < (uint64_t)RS_TILE ? (n - tile0) : (uint64_t)RS_TILE);
+  for (uint32_t i = threadIdx.x; i < cnt; i += RS_THREADS) {
+    const K key = sk[i];
+    const uint32_t dg = (uint32_t)(key >> shift) & 255u;
+    const uint64_t pos = gbase[dg] + (i - lstart[dg]);
+    kout[pos] = key;
+    if (vout) vout[pos] = sv[i];
   }
 }
 
