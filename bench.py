@@ -54,6 +54,24 @@ def measured_traffic(tag: str):
     return MEASURED_TRAFFIC["bytes"].get(tag)
 
 
+def max_over_ranks(x: float, dist=None) -> float:
+    """The largest x over all ranks (the timing rule: the job is as slow as its
+    slowest rank); x itself without a process group."""
+    if dist is None:
+        return x
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: float, ms: float) -> float:
+    """Units per second of the whole job: every rank processes units_per_rank
+    (replicas, weak scaling) within the slowest rank's ms."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def measured_peaks(key: str = "hbm_gbs"):
     """(peak, 'measured' | 'fallback') for hbm_gbs (GB/s) or a bf16 TFLOP/s key."""
     fallback = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
@@ -172,7 +190,7 @@ def run_reference(args, rank, world):
             vals.append(v)
     value = statistics.median(vals)
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "wedges/s", "n_gpus": 0,
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "wedges/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": W / value * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "W": int(W)},
@@ -261,11 +279,8 @@ def run_own(args, rank, world, local_rank):
     bfc.bfc_profile_enable(False)
     ms = e0.elapsed_time(e1) / args.steps
     prof = {t: bfc.bfc_profile_read(t) for t in bfc.PROFILE_TAGS}
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * W / (ms / 1e3)
+    ms = max_over_ranks(ms, dist)
+    value = whole_job_rate(world, W, ms)
 
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     hu = torch.from_numpy(g.u.astype(np.int32)).pin_memory()
@@ -290,18 +305,20 @@ def run_own(args, rank, world, local_rank):
             bfc.bfc_graph_free(h)
         torch.cuda.synchronize()
 
-    e2e_steps = max(2, min(args.steps, 5))
+    # every end-to-end step is timed on the host (each ends with a device
+    # synchronise, so its time holds its copies and its kernels); the median
+    # step is reported, since host-side allocation and copy times vary
+    e2e_steps = max(5, min(args.steps, 10))
     e2e_step()
     barrier()
-    t0 = time.perf_counter()
+    e2e_times = []
     for _ in range(e2e_steps):
+        t0 = time.perf_counter()
         e2e_step()
+        e2e_times.append((time.perf_counter() - t0) * 1e3)
     barrier()
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
-    if dist:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = float(np.median(e2e_times))
+    e2e_ms = max_over_ranks(e2e_ms, dist)
     assert int(obU.sum()) == 2 * Bval and int(obe.sum()) == 4 * Bval
 
     # ---- roofline of the dominant kernel
@@ -344,7 +361,8 @@ def run_own(args, rank, world, local_rank):
         "config": {"workload": WORKLOAD, "nU": nU, "nV": nV, "m": m, "W": W, "B": Bval, "start_side": "UV"[side],
                    "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (edge list 400 MB)",
                    "classes": ps["count"], "class_wedges": ps["work"]},
-        "e2e": {"value": world * W / (e2e_ms / 1e3), "unit": "wedges/s", "ms_per_step": e2e_ms,
+        "e2e": {"value": whole_job_rate(world, W, e2e_ms), "unit": "wedges/s", "ms_per_step": e2e_ms,
+                "ms_per_step_min_max": [min(e2e_times), max(e2e_times)], "steps_timed": e2e_steps,
                 "h2d_bytes_per_step": 8 * m, "d2h_bytes_per_step": 8 * (nU + nV + m) + 16},
         "gpu_launches": launches,
         "clocks": clk.summary(),
