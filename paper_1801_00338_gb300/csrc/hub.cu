@@ -15,7 +15,10 @@
 // A hub's later vertices (rank order) are all hubs, so the block counts every
 // pair whose first vertex is a hub; the window kernels skip hub start vertices
 // and count all other pairs as before.
+#include <cuda.h>  // CUtensorMap and the tensor-map encoder's signature (reached through the runtime)
+
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "bfc_internal.cuh"
@@ -24,12 +27,12 @@ namespace bfc {
 namespace {
 
 constexpr int TM = 128;          // tile rows / columns
-constexpr int KC = 64;           // K elements per staged chunk (4 MMAs of K = 16)
+constexpr int KC = 64;           // K elements per chunk (4 MMAs of K = 16)
 constexpr int HB_THREADS = 128;  // one warpgroup
-constexpr int HB_PER_SM = 4;     // 4 x 128 TMEM columns = 512
+constexpr int HB_PER_SM = 3;     // 3 x 64 KB of operand stages; 3 x 128 TMEM columns
 constexpr uint64_t WAIT_NS = 1000000000ull;  // bounded waits give up after ~1 s
-constexpr size_t HB_SMEM = 52 * 1024;     // 32 KB of operands, sized so at most 4 CTAs share an SM
-                                          // (4 x 128 TMEM columns = all 512)
+constexpr uint32_t STAGE_BYTES = 2 * TM * KC * 2;  // A_i and A_j chunks, 16 KB each
+constexpr size_t HB_SMEM = 2 * STAGE_BYTES + 1024;  // two stages, plus room to align them to 1 KB
 
 unsigned hb_grid(uint64_t n, unsigned threads, unsigned cap = 152 * 16) {
   uint64_t g = (n + threads - 1) / threads;
@@ -40,12 +43,11 @@ unsigned hb_grid(uint64_t n, unsigned threads, unsigned cap = 152 * 16) {
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// K-major operand layout without swizzle: 8-row x 16-byte core matrices; the
-// core matrix of rows 8g.. and elements 8c.. sits at g * SBO + c * LBO.
-constexpr uint32_t LBO = 128, SBO = (KC / 8) * 128;
-__device__ __forceinline__ uint32_t core_off(int row, int kgroup) {
-  return (uint32_t)((row >> 3) * SBO + kgroup * LBO + (row & 7) * 16);
-}
+// K-major operand layout without swizzle: 8-row x 16-byte core matrices.  A
+// TMA box of 8 elements x 128 rows lands as one column of 16 core matrices
+// (2 KB, rows 16 bytes apart), and the chunk's 8 columns follow one another,
+// so the core matrix of rows 8g.. and elements 8c.. sits at g * SBO + c * LBO.
+constexpr uint32_t LBO = 2048, SBO = 128;
 
 // shared memory matrix descriptor (tcgen05): start, leading and stride byte
 // offsets in 16-byte units, descriptor version 1, no swizzle
@@ -155,78 +157,112 @@ __device__ __forceinline__ uint32_t mbar_wait_bounded(uint32_t bar, uint32_t par
   }
 }
 
-// One CTA (one warpgroup) per tile at a time, tiles from a global queue.
-// Per 64-wide K chunk: the CTA stages A_i and A_j rows into the canonical
-// K-major layout, one thread issues four 128x128x16 MMAs into the CTA's 128
-// TMEM columns and commits them to an mbarrier, and all threads wait for it
-// before the chunk's buffers are refilled.  The epilogue reads the 128 x 128
-// fp32 accumulator (TMEM lane = tile row), adds C_L and sums C(c, 2).
-__global__ void __launch_bounds__(HB_THREADS) k_hub_mma(const uint16_t *A, uint32_t Kp, uint32_t h,
-                                                        const unsigned int *CL, unsigned int *queue,
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// One CTA (one warpgroup) per 128 x 128 tile at a time, tiles from a global
+// queue.  Thread 0 runs the main loop: for each 64-wide K chunk it loads the
+// A_i and A_j chunks with 16 TMA copies into one of two stages (the next
+// chunk's copies are issued before the current chunk's MMAs, so loading and
+// multiplying overlap), waits for them on the stage's `full` barrier, issues
+// four 128x128x16 MMAs into the tile's fp32 accumulator in tensor memory and
+// commits them to the stage's `empty` barrier, which frees the stage.  After
+// the last chunk a commit to `done` releases the epilogue: the 4 warps read
+// the accumulator (TMEM lane = tile row), add C_L and sum C(c, 2).
+__global__ void __launch_bounds__(HB_THREADS) k_hub_mma(const __grid_constant__ CUtensorMap amap, uint32_t Kp,
+                                                        uint32_t h, const unsigned int *CL, unsigned int *queue,
                                                         unsigned long long *B, uint32_t *err) {
-  extern __shared__ __align__(1024) uint8_t hub_smem[];
-  uint8_t *sa = hub_smem, *sb = hub_smem + TM * KC * 2;
-  __shared__ __align__(8) uint64_t mbar;
-  __shared__ uint32_t tmem_holder, sh_tile;
+  extern __shared__ uint8_t hub_smem[];
+  __shared__ __align__(8) uint64_t full[2], empty[2], done;
+  __shared__ uint32_t tmem_holder, sh_tile, sh_ok;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // the stages start at the first 1 KB boundary of the dynamic buffer
+  const uint32_t st0 = (smem_u32(hub_smem) + 1023u) & ~1023u;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
                  "r"(TM));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
+    for (int i = 0; i < 2; i++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[i])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[i])), "r"(1));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&done)), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;");
+    sh_ok = 1;
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t taddr = tmem_holder;
   const uint32_t nt = h / TM, ntiles = nt * (nt + 1) / 2, nchunks = Kp / KC;
-  uint32_t phase = 0;
-  bool ok = true;
+  uint32_t q = 0;      // chunks issued so far by this CTA (thread 0): stage q & 1, its use q >> 1
+  uint32_t ntile = 0;  // tiles finished by this CTA
   unsigned long long acc = 0;
-  while (ok) {
-    if (tid == 0) sh_tile = atomicAdd(queue, 1u);
+  // copy chunk c of tile (ti, tj) into the stage of chunk number qn
+  auto issue = [&](uint32_t qn, uint32_t c, uint32_t ti, uint32_t tj) {
+    const uint32_t stage = st0 + (qn & 1) * STAGE_BYTES, bar = smem_u32(&full[qn & 1]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(STAGE_BYTES));
+#pragma unroll
+    for (int g = 0; g < KC / 8; g++) {
+      const int x = (int)(c * KC + g * 8);
+      tma_load_2d(stage + g * LBO, &amap, x, (int)(ti * TM), bar);
+      tma_load_2d(stage + STAGE_BYTES / 2 + g * LBO, &amap, x, (int)(tj * TM), bar);
+    }
+  };
+  while (true) {
+    if (tid == 0) sh_tile = sh_ok ? atomicAdd(queue, 1u) : ntiles;
     __syncthreads();
     const uint32_t t = sh_tile;
     if (t >= ntiles) break;
     uint32_t ti, tj;
     tile_of(t, nt, ti, tj);
-    const uint16_t *Ai = A + (uint64_t)ti * TM * Kp, *Aj = A + (uint64_t)tj * TM * Kp;
-    for (uint32_t kc = 0; kc < nchunks; kc++) {
-      // stage: 8 threads per row, 16 bytes each (128-byte row pieces)
-      for (int q = tid; q < TM * (KC / 8); q += HB_THREADS) {
-        const int row = q >> 3, g = q & 7;
-        const uint64_t goff = (uint64_t)row * Kp + (uint64_t)kc * KC + g * 8;
-        *reinterpret_cast<uint4 *>(sa + core_off(row, g)) = __ldg(reinterpret_cast<const uint4 *>(Ai + goff));
-        *reinterpret_cast<uint4 *>(sb + core_off(row, g)) = __ldg(reinterpret_cast<const uint4 *>(Aj + goff));
-      }
-      asm volatile("fence.proxy.async.shared::cta;");
-      __syncthreads();
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      if (tid == 0) {
+    if (tid == 0) {
+      bool ok = true;
+      if (q >= 2) ok = mbar_wait_bounded(smem_u32(&empty[q & 1]), ((q - 2) >> 1) & 1);
+      if (ok) issue(q, 0, ti, tj);
+      for (uint32_t c = 0; c < nchunks && ok; c++) {
+        const uint32_t qc = q + c;
+        if (c + 1 < nchunks) {
+          const uint32_t qn = qc + 1;  // its stage was last read by chunk qn - 2
+          if (qn >= 2 && !mbar_wait_bounded(smem_u32(&empty[qn & 1]), ((qn - 2) >> 1) & 1)) { ok = false; break; }
+          issue(qn, c + 1, ti, tj);
+        }
+        if (!mbar_wait_bounded(smem_u32(&full[qc & 1]), (qc >> 1) & 1)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t stage = st0 + (qc & 1) * STAGE_BYTES;
 #pragma unroll
         for (int k = 0; k < KC / 16; k++) {
-          const uint64_t ad = smem_desc(smem_u32(sa) + k * 2 * LBO);
-          const uint64_t bd = smem_desc(smem_u32(sb) + k * 2 * LBO);
-          const uint32_t accum = (kc > 0 || k > 0) ? 1u : 0u;
+          const uint64_t ad = smem_desc(stage + k * 2 * LBO);
+          const uint64_t bd = smem_desc(stage + STAGE_BYTES / 2 + k * 2 * LBO);
+          const uint32_t accum = (c > 0 || k > 0) ? 1u : 0u;
           asm volatile(
               "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
               "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr),
               "l"(ad), "l"(bd), "r"(IDESC), "r"(accum));
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_u32(&mbar)));
+            smem_u32(&empty[qc & 1])));
       }
-      const uint32_t done = mbar_wait_bounded(smem_u32(&mbar), phase);
-      phase ^= 1;
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      ok = __syncthreads_and(done) != 0;  // uniform across the CTA
-      if (!ok) break;
+      q += nchunks;
+      // `done` completes when every MMA issued so far has finished
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&done)));
+      if (!ok) {
+        sh_ok = 0;
+        atomicOr(err, DERR_TIMEOUT);
+      }
     }
-    if (!ok) {
-      if (tid == 0) atomicOr(err, DERR_TIMEOUT);
+    const uint32_t fin = mbar_wait_bounded(smem_u32(&done), ntile & 1);
+    ntile++;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (__syncthreads_and(fin) == 0 || !sh_ok) {
+      if (tid == 0) { sh_ok = 0; atomicOr(err, DERR_TIMEOUT); }
       break;
     }
     // epilogue: row i of the tile is TMEM lane i; sum C(c, 2) over global i < j
@@ -239,20 +275,15 @@ __global__ void __launch_bounds__(HB_THREADS) k_hub_mma(const uint16_t *A, uint3
                    : "r"(ta));
       asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-      for (int q = 0; q < 8; q++) {
-        const uint32_t gj = tj * TM + c0 + q;
+      for (int k = 0; k < 8; k++) {
+        const uint32_t gj = tj * TM + c0 + k;
         if (gj <= gi) continue;
-        const uint64_t c = (uint64_t)__uint_as_float(r[q]) + CL[(uint64_t)gi * h + gj];
+        const uint64_t c = (uint64_t)__uint_as_float(r[k]) + CL[(uint64_t)gi * h + gj];
         if (c > 1) acc += c * (c - 1) / 2;
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-  }
-  if (!ok) {
-    // a commit that never arrived: give the MMAs in flight one more bounded
-    // wait before the columns are released
-    mbar_wait_bounded(smem_u32(&mbar), phase ^ 1);
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if (lane == 0 && acc) atomicAdd(B, acc);
@@ -267,6 +298,39 @@ __global__ void k_min_rank(const uint32_t *list, uint32_t n, unsigned int *out) 
     mine = min(mine, list[i]);
   for (int o = 16; o > 0; o >>= 1) mine = min(mine, __shfl_down_sync(0xffffffffu, mine, o));
   if ((threadIdx.x & 31) == 0 && mine != 0xFFFFFFFFu) atomicMin(out, mine);
+}
+
+// cuTensorMapEncodeTiled, reached through the runtime's driver entry point
+// (no link against the driver library)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+// tensor map of A_H (h rows of Kp bf16 values, row-major): boxes of 8
+// elements x 128 rows, i.e. one column of 16 core matrices
+int hub_tensor_map(CUtensorMap *map, void *A, uint32_t h, uint32_t Kp) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return BFC_ECUDA;
+  const cuuint64_t dims[2] = {Kp, h};
+  const cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+  const cuuint32_t box[2] = {8, (cuuint32_t)TM};
+  const cuuint32_t es[2] = {1, 1};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, A, dims, strides, box, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? BFC_OK : BFC_ECUDA;
 }
 
 int sm_count_hub() {
@@ -384,10 +448,11 @@ int hub_block_count(bfc_graph *g, Plan &p, uint32_t h, uint32_t tau, unsigned lo
   }
   const uint64_t ntiles = (uint64_t)(h / TM) * (h / TM + 1) / 2;
   const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)sm_count_hub() * HB_PER_SM, ntiles);
+  CUtensorMap amap;
+  HB_TRY(hub_tensor_map(&amap, A.p, h, Kp));
   HB_CUDA(cudaFuncSetAttribute(k_hub_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HB_SMEM));
   profile_begin("hub.total", s);
-  k_hub_mma<<<grid, HB_THREADS, HB_SMEM, s>>>(ptr<uint16_t>(A), Kp, h, ptr<unsigned int>(CL), queue, d_B,
-                                              ptr<uint32_t>(g->err));
+  k_hub_mma<<<grid, HB_THREADS, HB_SMEM, s>>>(amap, Kp, h, ptr<unsigned int>(CL), queue, d_B, ptr<uint32_t>(g->err));
   count_launch();
   profile_end("hub.total", s);
   HB_CUDA(cudaGetLastError());
