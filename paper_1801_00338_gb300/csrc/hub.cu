@@ -29,10 +29,12 @@ namespace {
 constexpr int TM = 128;          // tile rows / columns
 constexpr int KC = 64;           // K elements per chunk (4 MMAs of K = 16)
 constexpr int HB_THREADS = 128;  // one warpgroup
-constexpr int HB_PER_SM = 3;     // 3 x 64 KB of operand stages; 3 x 128 TMEM columns
+constexpr int SW = 4;            // tiles per strip: (ti, tj .. tj + 3) share the A_i chunk
+constexpr int HB_PER_SM = 1;     // one CTA per SM: 4 x 128 TMEM columns, 2 x 80 KB of stages
 constexpr uint64_t WAIT_NS = 1000000000ull;  // bounded waits give up after ~1 s
-constexpr uint32_t STAGE_BYTES = 2 * TM * KC * 2;  // A_i and A_j chunks, 16 KB each
-constexpr size_t HB_SMEM = 2 * STAGE_BYTES + 1024;  // two stages, plus room to align them to 1 KB
+constexpr uint32_t OP_BYTES = TM * KC * 2;                 // one 128 x 64 operand chunk, 16 KB
+constexpr uint32_t STAGE_BYTES = (1 + SW) * OP_BYTES;      // A_i and up to four A_j chunks
+constexpr size_t HB_SMEM = 2 * STAGE_BYTES + 1024;         // two stages, plus room to align them to 1 KB
 
 unsigned hb_grid(uint64_t n, unsigned threads, unsigned cap = 152 * 16) {
   uint64_t g = (n + threads - 1) / threads;
@@ -43,17 +45,19 @@ unsigned hb_grid(uint64_t n, unsigned threads, unsigned cap = 152 * 16) {
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// K-major operand layout without swizzle: 8-row x 16-byte core matrices.  A
-// TMA box of 8 elements x 128 rows lands as one column of 16 core matrices
-// (2 KB, rows 16 bytes apart), and the chunk's 8 columns follow one another,
-// so the core matrix of rows 8g.. and elements 8c.. sits at g * SBO + c * LBO.
-constexpr uint32_t LBO = 2048, SBO = 128;
+// K-major operand layout with the 128-byte swizzle: a TMA box of 64 elements x
+// 128 rows lands as 128 rows of 128 bytes, the 16-byte pieces of row r placed
+// at piece ^ (r & 7); 8-row groups are 1,024 bytes apart (SBO), and the K step
+// of 16 elements moves the descriptor's start by 32 bytes.  Operand bases are
+// 1,024-byte aligned.
+constexpr uint32_t LBO = 16, SBO = 1024;
+constexpr uint32_t KSTEP_BYTES = 32;
 
 // shared memory matrix descriptor (tcgen05): start, leading and stride byte
-// offsets in 16-byte units, descriptor version 1, no swizzle
+// offsets in 16-byte units, descriptor version 1, layout type 2 (128-byte swizzle)
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((LBO >> 4) & 0x3FFF) << 16) |
-         ((uint64_t)((SBO >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+         ((uint64_t)((SBO >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
 // instruction descriptor: D fp32, A and B bf16, both K-major, M = N = 128
@@ -131,12 +135,13 @@ __global__ void k_light_pairs(const uint64_t *offM, const uint32_t *mR, const ui
 // ---------------------------------------------------------------------------
 // tensor-core tiles: C_ij = A_i A_j^T over upper-triangle tile pairs (ti <= tj)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void tile_of(uint32_t t, uint32_t nt, uint32_t &ti, uint32_t &tj) {
-  // enumerate (ti, tj), ti <= tj, row by row
+// strip t: tile row ti and its first tile column tj0 (row ti has
+// ceil((nt - ti) / SW) strips, tj0 = ti, ti + SW, ...)
+__device__ __forceinline__ void strip_of(uint32_t t, uint32_t nt, uint32_t &ti, uint32_t &tj0) {
   uint32_t i = 0, rem = t;
-  while (rem >= nt - i) { rem -= nt - i; i++; }
+  while (rem >= (nt - i + SW - 1) / SW) { rem -= (nt - i + SW - 1) / SW; i++; }
   ti = i;
-  tj = i + rem;
+  tj0 = i + rem * SW;
 }
 
 // Wait for phase `parity` of an mbarrier for at most about one second of
@@ -164,27 +169,28 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
       : "memory");
 }
 
-// One CTA (one warpgroup) per 128 x 128 tile at a time, tiles from a global
-// queue.  Thread 0 runs the main loop: for each 64-wide K chunk it loads the
-// A_i and A_j chunks with 16 TMA copies into one of two stages (the next
-// chunk's copies are issued before the current chunk's MMAs, so loading and
-// multiplying overlap), waits for them on the stage's `full` barrier, issues
-// four 128x128x16 MMAs into the tile's fp32 accumulator in tensor memory and
+// One CTA (one warpgroup) per SM, strips of up to four 128 x 128 tiles
+// (ti, tj0 .. tj0 + 3) from a global queue; the four accumulators fill the
+// SM's 512 TMEM columns.  Thread 0 runs the main loop: for each 64-wide K chunk
+// it loads the A_i chunk and the strip's A_j chunks with TMA (one 64 x 128
+// copy each) into one of two stages, issuing the next chunk's copies before
+// the current chunk's MMAs so that loading and multiplying overlap; waits for
+// them on the stage's `full` barrier; issues 4 x 4 MMAs of 128x128x16; and
 // commits them to the stage's `empty` barrier, which frees the stage.  After
 // the last chunk a commit to `done` releases the epilogue: the 4 warps read
-// the accumulator (TMEM lane = tile row), add C_L and sum C(c, 2).
+// each accumulator (TMEM lane = tile row), add C_L and sum C(c, 2) over i < j.
 __global__ void __launch_bounds__(HB_THREADS) k_hub_mma(const __grid_constant__ CUtensorMap amap, uint32_t Kp,
                                                         uint32_t h, const unsigned int *CL, unsigned int *queue,
                                                         unsigned long long *B, uint32_t *err) {
   extern __shared__ uint8_t hub_smem[];
   __shared__ __align__(8) uint64_t full[2], empty[2], done;
-  __shared__ uint32_t tmem_holder, sh_tile, sh_ok;
+  __shared__ uint32_t tmem_holder, sh_item, sh_ok;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // the stages start at the first 1 KB boundary of the dynamic buffer
   const uint32_t st0 = (smem_u32(hub_smem) + 1023u) & ~1023u;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
-                 "r"(TM));
+                 "r"(SW * TM));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
@@ -200,51 +206,53 @@ __global__ void __launch_bounds__(HB_THREADS) k_hub_mma(const __grid_constant__ 
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t taddr = tmem_holder;
-  const uint32_t nt = h / TM, ntiles = nt * (nt + 1) / 2, nchunks = Kp / KC;
+  const uint32_t nt = h / TM, nchunks = Kp / KC;
+  uint32_t nitems = 0;
+  for (uint32_t i = 0; i < nt; i++) nitems += (nt - i + SW - 1) / SW;
   uint32_t q = 0;      // chunks issued so far by this CTA (thread 0): stage q & 1, its use q >> 1
-  uint32_t ntile = 0;  // tiles finished by this CTA
+  uint32_t nfin = 0;   // strips finished by this CTA
   unsigned long long acc = 0;
-  // copy chunk c of tile (ti, tj) into the stage of chunk number qn
-  auto issue = [&](uint32_t qn, uint32_t c, uint32_t ti, uint32_t tj) {
+  // copy chunk c of the strip into the stage of chunk number qn
+  auto issue = [&](uint32_t qn, uint32_t c, uint32_t ti, uint32_t tj0, uint32_t w) {
     const uint32_t stage = st0 + (qn & 1) * STAGE_BYTES, bar = smem_u32(&full[qn & 1]);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(STAGE_BYTES));
-#pragma unroll
-    for (int g = 0; g < KC / 8; g++) {
-      const int x = (int)(c * KC + g * 8);
-      tma_load_2d(stage + g * LBO, &amap, x, (int)(ti * TM), bar);
-      tma_load_2d(stage + STAGE_BYTES / 2 + g * LBO, &amap, x, (int)(tj * TM), bar);
-    }
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"((1 + w) * OP_BYTES));
+    const int x = (int)(c * KC);
+    tma_load_2d(stage, &amap, x, (int)(ti * TM), bar);
+    for (uint32_t t = 0; t < w; t++) tma_load_2d(stage + (1 + t) * OP_BYTES, &amap, x, (int)((tj0 + t) * TM), bar);
   };
   while (true) {
-    if (tid == 0) sh_tile = sh_ok ? atomicAdd(queue, 1u) : ntiles;
+    if (tid == 0) sh_item = sh_ok ? atomicAdd(queue, 1u) : nitems;
     __syncthreads();
-    const uint32_t t = sh_tile;
-    if (t >= ntiles) break;
-    uint32_t ti, tj;
-    tile_of(t, nt, ti, tj);
+    const uint32_t it = sh_item;
+    if (it >= nitems) break;
+    uint32_t ti, tj0;
+    strip_of(it, nt, ti, tj0);
+    const uint32_t w = min((uint32_t)SW, nt - tj0);  // tiles in this strip
     if (tid == 0) {
       bool ok = true;
       if (q >= 2) ok = mbar_wait_bounded(smem_u32(&empty[q & 1]), ((q - 2) >> 1) & 1);
-      if (ok) issue(q, 0, ti, tj);
+      if (ok) issue(q, 0, ti, tj0, w);
       for (uint32_t c = 0; c < nchunks && ok; c++) {
         const uint32_t qc = q + c;
         if (c + 1 < nchunks) {
           const uint32_t qn = qc + 1;  // its stage was last read by chunk qn - 2
           if (qn >= 2 && !mbar_wait_bounded(smem_u32(&empty[qn & 1]), ((qn - 2) >> 1) & 1)) { ok = false; break; }
-          issue(qn, c + 1, ti, tj);
+          issue(qn, c + 1, ti, tj0, w);
         }
         if (!mbar_wait_bounded(smem_u32(&full[qc & 1]), (qc >> 1) & 1)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint32_t stage = st0 + (qc & 1) * STAGE_BYTES;
 #pragma unroll
         for (int k = 0; k < KC / 16; k++) {
-          const uint64_t ad = smem_desc(stage + k * 2 * LBO);
-          const uint64_t bd = smem_desc(stage + STAGE_BYTES / 2 + k * 2 * LBO);
+          const uint64_t ad = smem_desc(stage + k * KSTEP_BYTES);
           const uint32_t accum = (c > 0 || k > 0) ? 1u : 0u;
-          asm volatile(
-              "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr),
-              "l"(ad), "l"(bd), "r"(IDESC), "r"(accum));
+          for (uint32_t t = 0; t < w; t++) {
+            const uint64_t bd = smem_desc(stage + (1 + t) * OP_BYTES + k * KSTEP_BYTES);
+            asm volatile(
+                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr + t * TM),
+                "l"(ad), "l"(bd), "r"(IDESC), "r"(accum));
+          }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
             smem_u32(&empty[qc & 1])));
@@ -258,28 +266,31 @@ __global__ void __launch_bounds__(HB_THREADS) k_hub_mma(const __grid_constant__ 
         atomicOr(err, DERR_TIMEOUT);
       }
     }
-    const uint32_t fin = mbar_wait_bounded(smem_u32(&done), ntile & 1);
-    ntile++;
+    const uint32_t fin = mbar_wait_bounded(smem_u32(&done), nfin & 1);
+    nfin++;
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (__syncthreads_and(fin) == 0 || !sh_ok) {
       if (tid == 0) { sh_ok = 0; atomicOr(err, DERR_TIMEOUT); }
       break;
     }
-    // epilogue: row i of the tile is TMEM lane i; sum C(c, 2) over global i < j
+    // epilogue: row i of each tile is TMEM lane i; sum C(c, 2) over global i < j
     const uint32_t gi = ti * TM + 32 * warp + lane;
-    for (int c0 = 0; c0 < TM; c0 += 8) {
-      uint32_t r[8];
-      const uint32_t ta = taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
-      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                   : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                   : "r"(ta));
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
+    for (uint32_t t = 0; t < w; t++) {
+      const uint32_t tj = tj0 + t;
+      for (int c0 = 0; c0 < TM; c0 += 8) {
+        uint32_t r[8];
+        const uint32_t ta = taddr + ((uint32_t)(32 * warp) << 16) + t * TM + (uint32_t)c0;
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                     : "r"(ta));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-      for (int k = 0; k < 8; k++) {
-        const uint32_t gj = tj * TM + c0 + k;
-        if (gj <= gi) continue;
-        const uint64_t c = (uint64_t)__uint_as_float(r[k]) + CL[(uint64_t)gi * h + gj];
-        if (c > 1) acc += c * (c - 1) / 2;
+        for (int k = 0; k < 8; k++) {
+          const uint32_t gj = tj * TM + c0 + k;
+          if (gj <= gi) continue;
+          const uint64_t c = (uint64_t)__uint_as_float(r[k]) + CL[(uint64_t)gi * h + gj];
+          if (c > 1) acc += c * (c - 1) / 2;
+        }
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -289,7 +300,7 @@ __global__ void __launch_bounds__(HB_THREADS) k_hub_mma(const __grid_constant__ 
   if (lane == 0 && acc) atomicAdd(B, acc);
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TM));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(SW * TM));
 }
 
 __global__ void k_min_rank(const uint32_t *list, uint32_t n, unsigned int *out) {
@@ -318,17 +329,17 @@ EncodeTiledFn encode_tiled() {
   return fn;
 }
 
-// tensor map of A_H (h rows of Kp bf16 values, row-major): boxes of 8
-// elements x 128 rows, i.e. one column of 16 core matrices
+// tensor map of A_H (h rows of Kp bf16 values, row-major): boxes of 64
+// elements x 128 rows, written to shared memory with the 128-byte swizzle
 int hub_tensor_map(CUtensorMap *map, void *A, uint32_t h, uint32_t Kp) {
   EncodeTiledFn fn = encode_tiled();
   if (!fn) return BFC_ECUDA;
   const cuuint64_t dims[2] = {Kp, h};
   const cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
-  const cuuint32_t box[2] = {8, (cuuint32_t)TM};
+  const cuuint32_t box[2] = {(cuuint32_t)KC, (cuuint32_t)TM};
   const cuuint32_t es[2] = {1, 1};
   const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, A, dims, strides, box, es,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? BFC_OK : BFC_ECUDA;
 }
@@ -446,8 +457,9 @@ int hub_block_count(bfc_graph *g, Plan &p, uint32_t h, uint32_t tau, unsigned lo
     count_launch();
     profile_end("hub.light", s);
   }
-  const uint64_t ntiles = (uint64_t)(h / TM) * (h / TM + 1) / 2;
-  const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)sm_count_hub() * HB_PER_SM, ntiles);
+  uint64_t nitems = 0;
+  for (uint32_t i = 0; i < h / TM; i++) nitems += (h / TM - i + SW - 1) / SW;
+  const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)sm_count_hub() * HB_PER_SM, nitems);
   CUtensorMap amap;
   HB_TRY(hub_tensor_map(&amap, A.p, h, Kp));
   HB_CUDA(cudaFuncSetAttribute(k_hub_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HB_SMEM));
