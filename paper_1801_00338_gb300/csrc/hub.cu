@@ -413,15 +413,16 @@ int hub_block_count(bfc_graph *g, Plan &p, uint32_t h, uint32_t tau, unsigned lo
     profile_end("hub.degree", s);
   }
   if (tau == 0) {
-    // cost model: a dense column costs every tile 2 x 128 x 2 bytes of operand
-    // staging (L2-resident A_H) plus its MMA work; a light column costs
-    // C(d, 2) scattered atomics.  Columns lumped in the last bin stay dense.
+    // cost model: a dense column costs every tile its share of the tile
+    // kernel (operand copies and MMAs, at the kernel's measured rate); a light
+    // column costs C(d, 2) scattered atomics.  Columns lumped in the last bin
+    // stay dense.
     std::vector<unsigned int> hh(HIST);
     HB_CUDA(cudaMemcpyAsync(hh.data(), hist.p, HIST * 4, cudaMemcpyDeviceToHost, s));
     HB_CUDA(cudaStreamSynchronize(s));
     const double tiles = (double)(h / TM) * (h / TM + 1) / 2;
-    const double per_col = tiles * (512.0 / 4.0e12 + 2.0 * TM * TM / 1.5e15);
-    const double per_pair = 1.0 / 1.5e11;
+    const double per_col = tiles * 4.0e-11;  // measured: 7.7 ms for 8,256 tiles x 22,974 columns
+    const double per_pair = 1.0 / 1.1e11;    // measured: 1.07 ms for 1.19e8 light pairs
     std::vector<double> cols_ge(HIST + 1, 0.0), pairs_lt(HIST + 1, 0.0);
     for (int d = HIST - 1; d >= 0; d--) cols_ge[d] = cols_ge[d + 1] + hh[d];
     for (uint32_t d = 1; d <= HIST; d++) pairs_lt[d] = pairs_lt[d - 1] + (double)hh[d - 1] * (d - 1) * (d - 2) / 2.0;
