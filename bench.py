@@ -40,8 +40,8 @@ CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.a
 # DRAM bytes (read + write) per call of each counting-kernel set, from one ncu
 # capture of this workload (profiles/win_edge_chung_lu_1m_5m.md), valid only
 # for the kernel source they were taken with (its SHA-256 prefix).
-MEASURED_TRAFFIC = {"source_sha256": "7d7305d7323b8293",
-                    "bytes": {"win.edge": 17.01e9, "win.total": 5.69e9, "big.edge": 7.36e9}}
+MEASURED_TRAFFIC = {"source_sha256": "05f8d735689b89d0",
+                    "bytes": {"win.edge": 17.055e9, "win.total": 5.703e9, "big.edge": 7.366e9}}
 
 
 def measured_traffic(tag: str):
