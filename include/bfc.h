@@ -89,6 +89,22 @@ typedef struct bfc_proposal bfc_proposal;
 int bfc_graph_from_edges(const uint32_t *u, const uint32_t *v, uint64_t m, uint32_t nU, uint32_t nV,
                          uint32_t flags, void *stream, bfc_graph **out);
 
+/* Build a graph from compressed rows already on the device (the caller keeps
+ * its arrays; the library copies and checks them).  Same graph as
+ * bfc_graph_from_edges on the same edge set.
+ *   offU (nU + 1 u64), nbrU (m u32): U rows, V ids strictly ascending in each
+ *     row; the canonical id of an edge is its position in nbrU.
+ *   offV (nV + 1 u64), nbrV (m u32): V rows, U ids strictly ascending.
+ *   eidV (m u32, may be NULL): canonical id of each V-row entry (computed,
+ *     or checked when given).
+ * m = offU[nU] = offV[nV].
+ * Errors: BFC_EINVAL (null pointers, nU or nV == 0, offsets that do not start
+ * at 0, decrease or disagree on m, a row not strictly ascending, the two
+ * sides not holding the same edges, eidV inconsistent with the rows),
+ * BFC_ERANGE (an id out of range, m >= 2^32), BFC_ENOMEM, BFC_ECUDA. */
+int bfc_graph_from_csr(const uint64_t *offU, const uint32_t *nbrU, uint32_t nU, const uint64_t *offV,
+                       const uint32_t *nbrV, const uint32_t *eidV, uint32_t nV, void *stream, bfc_graph **out);
+
 /* Release a graph and its device memory (after work on its stream is done). */
 int bfc_graph_free(bfc_graph *g);
 

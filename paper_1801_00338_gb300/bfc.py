@@ -52,6 +52,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     sig = {
         "bfc_graph_from_edges": [P, P, u64, u32, u32, u32, P, P],
         "bfc_graph_free": [P],
+        "bfc_graph_from_csr": [P, P, u32, P, P, P, u32, P, P],
         "bfc_graph_stats": [P, P, P, P, P, P],
         "bfc_graph_edges": [P, P, P, P],
         "bfc_exact": [P, u32, P, P, P],
@@ -190,6 +191,15 @@ def bfc_graph_from_edges(u, v, nU: int, nV: int, flags: int = 0, stream=None) ->
         rc = L.bfc_graph_from_edges(u.ctypes.data, v.ctypes.data, u.size, nU, nV, flags & ~BFC_INPUT_DEVICE,
                                     _stream_ptr(stream), ctypes.byref(h))
     _check(rc, "bfc_graph_from_edges")
+    return h.value
+
+
+def bfc_graph_from_csr(offU, nbrU, nU: int, offV, nbrV, nV: int, eidV=None, stream=None) -> int:
+    """Build a graph from device rows (int64 offsets, int32 ids as CUDA tensors)."""
+    h = ctypes.c_void_p()
+    _check(load().bfc_graph_from_csr(_dptr(offU), _dptr(nbrU), nU, _dptr(offV), _dptr(nbrV),
+                                     _dptr(eidV) if eidV is not None else None, nV, _stream_ptr(stream),
+                                     ctypes.byref(h)), "bfc_graph_from_csr")
     return h.value
 
 
@@ -459,6 +469,16 @@ class Graph:
         self.h = bfc_graph_from_edges(u, v, nU, nV, BFC_DEDUP if dedup else 0, stream)
         self.stats = bfc_graph_stats(self.h)
         self.m = self.stats["m"]
+
+    @classmethod
+    def from_csr(cls, offU, nbrU, nU: int, offV, nbrV, nV: int, eidV=None, stream=None):
+        """A graph from device rows (bfc_graph_from_csr)."""
+        G = cls.__new__(cls)
+        G.nU, G.nV = int(nU), int(nV)
+        G.h = bfc_graph_from_csr(offU, nbrU, nU, offV, nbrV, nV, eidV, stream)
+        G.stats = bfc_graph_stats(G.h)
+        G.m = G.stats["m"]
+        return G
 
     def exact(self, side=None, hub_mma=False, stream=None):
         return bfc_exact(self.h, _SIDE[side] | (BFC_HUB_MMA if hub_mma else 0), stream)

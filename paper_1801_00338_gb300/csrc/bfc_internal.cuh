@@ -56,6 +56,7 @@ enum DeviceError : uint32_t {
   DERR_CAPACITY = 1u << 2,   // a table ran out of room (internal consistency)
   DERR_TIMEOUT = 1u << 3,    // a bounded wait gave up
   DERR_OVERFLOW = 1u << 4,   // a counter would have wrapped
+  DERR_INVALID = 1u << 5,    // malformed input rows (order, offsets, edge ids)
 };
 
 // ---------------------------------------------------------------------------
@@ -152,6 +153,9 @@ struct bfc_graph {
 
 namespace bfc {
 int graph_build(bfc_graph *g, const uint32_t *u, const uint32_t *v, uint64_t m, uint32_t flags, cudaStream_t s);
+// The same graph from caller-owned device rows (copied and checked); eidV may be null.
+int graph_from_rows(bfc_graph *g, const uint64_t *offU, const uint32_t *nbrU, const uint64_t *offV,
+                    const uint32_t *nbrV, const uint32_t *eidV, cudaStream_t s);
 int plan_build(bfc_graph *g, int side, cudaStream_t s);
 int choose_side(const bfc_graph *g, uint32_t flags);
 int read_device_error(bfc_graph *g, cudaStream_t s);  // maps DERR_* bits to a status and clears

@@ -70,6 +70,25 @@ int bfc_graph_from_edges(const uint32_t *u, const uint32_t *v, uint64_t m, uint3
   return BFC_OK;
 }
 
+int bfc_graph_from_csr(const uint64_t *offU, const uint32_t *nbrU, uint32_t nU, const uint64_t *offV,
+                       const uint32_t *nbrV, const uint32_t *eidV, uint32_t nV, void *stream, bfc_graph **out) {
+  if (!out || !offU || !nbrU || !offV || !nbrV || nU == 0 || nV == 0) return BFC_EINVAL;
+  *out = nullptr;
+  bfc_graph *g = new (std::nothrow) bfc_graph();
+  if (!g) return BFC_ENOMEM;
+  g->nU = nU;
+  g->nV = nV;
+  cudaStream_t s = as_stream(stream);
+  g->last_stream = s;
+  int rc = graph_from_rows(g, offU, nbrU, offV, nbrV, eidV, s);
+  if (rc != BFC_OK) {
+    bfc_graph_free(g);
+    return rc;
+  }
+  *out = g;
+  return BFC_OK;
+}
+
 int bfc_graph_free(bfc_graph *g) {
   if (!g) return BFC_EINVAL;
   cudaStream_t s = g->last_stream;

@@ -139,7 +139,26 @@ int read_device_error(bfc_graph *g, cudaStream_t s) {
   if (e & DERR_DUP) return BFC_EDUP;
   if (e & DERR_TIMEOUT) return BFC_ETIMEOUT;
   if (e & DERR_OVERFLOW) return BFC_EOVERFLOW;
+  if (e & DERR_INVALID) return BFC_EINVAL;
   return BFC_EINTERNAL;
+}
+
+// degrees, sum d^2, wedges C(d, 2) and maximum degree of both sides
+static int degree_stats(bfc_graph *g, cudaStream_t s) {
+  const uint32_t nU = g->nU, nV = g->nV;
+  BFC_CUDA_TRY(cudaMemsetAsync(g->acc.p, 0, 256, s));
+  unsigned long long *acc = ptr<unsigned long long>(g->acc);
+  k_degrees<<<grid_for(nU, 256), 256, 0, s>>>(ptr<uint64_t>(g->offU), nU, ptr<uint32_t>(g->degU), acc);
+  count_launch();
+  k_degrees<<<grid_for(nV, 256), 256, 0, s>>>(ptr<uint64_t>(g->offV), nV, ptr<uint32_t>(g->degV), acc + 4);
+  count_launch();
+  unsigned long long h[8];
+  BFC_CUDA_TRY(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
+  BFC_CUDA_TRY(cudaStreamSynchronize(s));
+  BFC_CUDA_TRY(cudaGetLastError());
+  g->sqU = h[0]; g->wU = h[1]; g->maxU = (uint32_t)h[2];
+  g->sqV = h[4]; g->wV = h[5]; g->maxV = (uint32_t)h[6];
+  return BFC_OK;
 }
 
 int graph_build(bfc_graph *g, const uint32_t *u, const uint32_t *v, uint64_t m, uint32_t flags, cudaStream_t s) {
@@ -230,22 +249,101 @@ int graph_build(bfc_graph *g, const uint32_t *u, const uint32_t *v, uint64_t m, 
   k_offsets_from_sorted32<<<grid_for(m + 1, 256), 256, 0, s>>>(ptr<uint32_t>(vk2), m, nV, ptr<uint64_t>(g->offV));
   count_launch();
   cleanup2();
-  // degree statistics
-  BFC_CUDA_TRY(cudaMemsetAsync(g->acc.p, 0, 256, s));
-  unsigned long long *acc = ptr<unsigned long long>(g->acc);
-  k_degrees<<<grid_for(nU, 256), 256, 0, s>>>(ptr<uint64_t>(g->offU), nU, ptr<uint32_t>(g->degU), acc);
-  count_launch();
-  k_degrees<<<grid_for(nV, 256), 256, 0, s>>>(ptr<uint64_t>(g->offV), nV, ptr<uint32_t>(g->degV), acc + 4);
-  count_launch();
-  unsigned long long h[8];
-  BFC_CUDA_TRY(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
-  BFC_CUDA_TRY(cudaStreamSynchronize(s));
-  BFC_CUDA_TRY(cudaGetLastError());
-  g->sqU = h[0]; g->wU = h[1]; g->maxU = (uint32_t)h[2];
-  g->sqV = h[4]; g->wV = h[5]; g->maxV = (uint32_t)h[6];
   cleanup();
 #undef GB_TRY
-  return BFC_OK;
+  return degree_stats(g, s);
+}
+
+// ---------------------------------------------------------------------------
+// graph from caller-owned rows
+// ---------------------------------------------------------------------------
+// offsets: start at 0, never decrease, end at m
+__global__ void k_check_offsets(const uint64_t *off, uint32_t n, uint64_t m, uint32_t *err) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    if (off[i] > off[i + 1] || off[i + 1] > m || (i == 0 && off[0] != 0)) atomicOr(err, DERR_INVALID);
+}
+// every entry below `bound`; strictly ascending within its row (one warp per row)
+__global__ void k_check_rows(const uint64_t *off, uint32_t n, const uint32_t *nbr, uint32_t bound, uint32_t *err) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t r = warp; r < n; r += nw) {
+    for (uint64_t i = off[r] + lane; i < off[r + 1]; i += 32) {
+      const uint32_t x = nbr[i];
+      if (x >= bound) atomicOr(err, DERR_RANGE);
+      if (i > off[r] && nbr[i - 1] >= x) atomicOr(err, DERR_INVALID);
+    }
+  }
+}
+// canonical id of each V-row entry (x's row holds a): the position of x in
+// a's ascending row; with `given` ids, check them instead
+__global__ void k_edge_ids(const uint64_t *offU, const uint32_t *nbrU, const uint64_t *offV, uint32_t nV,
+                           const uint32_t *nbrV, const uint32_t *given, uint32_t *eidV, uint32_t *err) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t x = warp; x < nV; x += nw) {
+    for (uint64_t i = offV[x] + lane; i < offV[x + 1]; i += 32) {
+      const uint32_t a = nbrV[i];
+      uint64_t lo = offU[a], hi = offU[a + 1];
+      while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (nbrU[mid] < x) lo = mid + 1; else hi = mid;
+      }
+      const bool found = lo < offU[a + 1] && nbrU[lo] == (uint32_t)x;
+      if (!found || (given && given[i] != lo)) atomicOr(err, DERR_INVALID);
+      eidV[i] = (uint32_t)lo;
+    }
+  }
+}
+
+int graph_from_rows(bfc_graph *g, const uint64_t *offU, const uint32_t *nbrU, const uint64_t *offV,
+                    const uint32_t *nbrV, const uint32_t *eidV, cudaStream_t s) {
+  const uint32_t nU = g->nU, nV = g->nV;
+  BFC_TRY(dalloc(g->err, 64, s));
+  BFC_CUDA_TRY(cudaMemsetAsync(g->err.p, 0, 64, s));
+  BFC_TRY(dalloc(g->acc, 256, s));
+  uint64_t mm[2];
+  BFC_CUDA_TRY(cudaMemcpyAsync(&mm[0], offU + nU, 8, cudaMemcpyDeviceToHost, s));
+  BFC_CUDA_TRY(cudaMemcpyAsync(&mm[1], offV + nV, 8, cudaMemcpyDeviceToHost, s));
+  BFC_CUDA_TRY(cudaStreamSynchronize(s));
+  if (mm[0] != mm[1]) return BFC_EINVAL;
+  const uint64_t m = mm[0];
+  if (m >= (1ull << 32)) return BFC_ERANGE;
+  g->m = m;
+  const uint64_t mb = std::max<uint64_t>(m, 1) * 4;
+  BFC_TRY(dalloc(g->offU, ((uint64_t)nU + 1) * 8, s));
+  BFC_TRY(dalloc(g->offV, ((uint64_t)nV + 1) * 8, s));
+  BFC_TRY(dalloc(g->nbrU, mb, s));
+  BFC_TRY(dalloc(g->nbrV, mb, s));
+  BFC_TRY(dalloc(g->eidV, mb, s));
+  BFC_TRY(dalloc(g->degU, (uint64_t)nU * 4, s));
+  BFC_TRY(dalloc(g->degV, (uint64_t)nV * 4, s));
+  BFC_CUDA_TRY(cudaMemcpyAsync(g->offU.p, offU, ((uint64_t)nU + 1) * 8, cudaMemcpyDeviceToDevice, s));
+  BFC_CUDA_TRY(cudaMemcpyAsync(g->offV.p, offV, ((uint64_t)nV + 1) * 8, cudaMemcpyDeviceToDevice, s));
+  if (m) {
+    BFC_CUDA_TRY(cudaMemcpyAsync(g->nbrU.p, nbrU, m * 4, cudaMemcpyDeviceToDevice, s));
+    BFC_CUDA_TRY(cudaMemcpyAsync(g->nbrV.p, nbrV, m * 4, cudaMemcpyDeviceToDevice, s));
+  }
+  uint32_t *err = ptr<uint32_t>(g->err);
+  k_check_offsets<<<grid_for(nU, 256), 256, 0, s>>>(ptr<uint64_t>(g->offU), nU, m, err);
+  count_launch();
+  k_check_offsets<<<grid_for(nV, 256), 256, 0, s>>>(ptr<uint64_t>(g->offV), nV, m, err);
+  count_launch();
+  BFC_TRY(read_device_error(g, s));  // the row checks below index by these offsets
+  k_check_rows<<<grid_for((uint64_t)nU * 32, 256), 256, 0, s>>>(ptr<uint64_t>(g->offU), nU, ptr<uint32_t>(g->nbrU),
+                                                               nV, err);
+  count_launch();
+  k_check_rows<<<grid_for((uint64_t)nV * 32, 256), 256, 0, s>>>(ptr<uint64_t>(g->offV), nV, ptr<uint32_t>(g->nbrV),
+                                                               nU, err);
+  count_launch();
+  BFC_TRY(read_device_error(g, s));  // ids in range before they index rows
+  k_edge_ids<<<grid_for((uint64_t)nV * 32, 256), 256, 0, s>>>(ptr<uint64_t>(g->offU), ptr<uint32_t>(g->nbrU),
+                                                             ptr<uint64_t>(g->offV), nV, ptr<uint32_t>(g->nbrV),
+                                                             eidV, ptr<uint32_t>(g->eidV), err);
+  count_launch();
+  BFC_TRY(read_device_error(g, s));
+  return degree_stats(g, s);
 }
 
 // Algorithm 1, first three lines: start from L (= U) unless sum_L d^2 < sum_R d^2.

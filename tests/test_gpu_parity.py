@@ -260,3 +260,65 @@ def test_batched_uneven_graphs_match_oracle(bfc):
     for (u, v, nU, nV), b, sd in zip(graphs, B, side):
         ob, os_ = O.exact(u, v, nU, nV)
         assert int(b) == ob and int(sd) == os_
+
+
+def _rows(u, v, nU, nV):
+    """Host CSR of both sides: U rows ascending in v (canonical order), V rows
+    ascending in u, and the canonical id of each V-row entry."""
+    order = np.lexsort((v, u))
+    cu, cv = u[order].astype(np.int64), v[order].astype(np.int64)
+    offU = np.zeros(nU + 1, np.int64)
+    np.add.at(offU, cu + 1, 1)
+    offU = np.cumsum(offU)
+    vo = np.lexsort((cu, cv))
+    offV = np.zeros(nV + 1, np.int64)
+    np.add.at(offV, cv + 1, 1)
+    offV = np.cumsum(offV)
+    return offU, cv.astype(np.int32), offV, cu[vo].astype(np.int32), vo.astype(np.int32)
+
+
+def test_graph_from_csr_matches_edge_list(bfc):
+    import torch
+    g = synth.chung_lu_scaled(3000, 9000, 60_000, 2.1, 2.4, 5)
+    offU, nbrU, offV, nbrV, eidV = _rows(g.u, g.v, g.nU, g.nV)
+    t = [torch.from_numpy(a).cuda() for a in (offU, nbrU, offV, nbrV, eidV)]
+    oB, _ = O.exact(g.u, g.v, g.nU, g.nV)
+    oU, oV = O.per_vertex(g.u, g.v, g.nU, g.nV)
+    with bfc.Graph(g.u, g.v, g.nU, g.nV) as G0:
+        e0, _ = G0.per_edge()
+        for eid in (None, t[4]):
+            G = bfc.Graph.from_csr(t[0], t[1], g.nU, t[2], t[3], g.nV, eidV=eid)
+            try:
+                assert G.stats == G0.stats
+                assert G.exact()[0] == oB and G.exact(hub_mma=True)[0] == oB
+                bU, bV, B = G.per_vertex()
+                assert B == oB and np.array_equal(u64(bU), oU) and np.array_equal(u64(bV), oV)
+                be, _ = G.per_edge()
+                assert np.array_equal(u64(be), u64(e0))   # same canonical order
+            finally:
+                G.close()
+
+
+def test_graph_from_csr_rejects_malformed_rows(bfc):
+    import torch
+    u, v = synth.uniform_bipartite(60, 50, 600, 3)
+    offU, nbrU, offV, nbrV, eidV = _rows(u, v, 60, 50)
+
+    def build(oU=offU, nU_=nbrU, oV=offV, nV_=nbrV, eid=None, nu=60, nv=50):
+        t = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (oU, nU_, oV, nV_)]
+        e = torch.from_numpy(np.ascontiguousarray(eid)).cuda() if eid is not None else None
+        bfc.bfc_graph_free(bfc.bfc_graph_from_csr(t[0], t[1], nu, t[2], t[3], nv, e))
+
+    build()
+    build(eid=eidV)
+    a = int(np.argmax(np.diff(offU) >= 2))          # a U row with two entries: swap them
+    bad = nbrU.copy()
+    bad[offU[a]], bad[offU[a] + 1] = bad[offU[a] + 1], bad[offU[a]]
+    cases = [(dict(nU_=bad), -1),                      # row not ascending
+             (dict(nU_=np.where(np.arange(nbrU.size) == 0, 50, nbrU).astype(np.int32)), -2),  # V id out of range
+             (dict(oV=np.concatenate([offV[:-1], [offV[-1] - 1]])), -1),   # the sides disagree on m
+             (dict(eid=np.roll(eidV, 1)), -1)]          # inconsistent edge ids
+    for kw, code in cases:
+        with pytest.raises(bfc.BfcError) as ei:
+            build(**kw)
+        assert ei.value.code == code, kw
