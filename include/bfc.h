@@ -320,6 +320,13 @@ int bfc_proposal_free(bfc_proposal *p);
  * the midpoint side (Lemma 2). */
 int bfc_plan_stats(bfc_graph *g, int side, uint64_t *out, void *stream);
 
+/* Device memory: every call allocates its temporaries from the library's own
+ * stream-ordered pool on the current device, which keeps freed memory for the
+ * next call instead of returning it (so repeated calls do not map new pages).
+ * bfc_trim_memory waits for the device and releases the pools' unused
+ * memory.  Errors: BFC_ECUDA. */
+int bfc_trim_memory(void);
+
 /* Device timing of the library's counting kernels: when enabled, every
  * wedge-kernel launch is bracketed by CUDA events on the launch stream.
  * bfc_profile_read synchronises on the recorded events and returns, for the

@@ -53,6 +53,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "bfc_graph_from_edges": [P, P, u64, u32, u32, u32, P, P],
         "bfc_graph_free": [P],
         "bfc_graph_from_csr": [P, P, u32, P, P, P, u32, P, P],
+        "bfc_trim_memory": [],
         "bfc_graph_stats": [P, P, P, P, P, P],
         "bfc_graph_edges": [P, P, P, P],
         "bfc_exact": [P, u32, P, P, P],
@@ -125,6 +126,10 @@ def _stream_ptr(stream) -> int | None:
 
 def _dptr(t) -> int:
     return t.data_ptr()
+
+
+def bfc_trim_memory():
+    _check(load().bfc_trim_memory(), "bfc_trim_memory")
 
 
 def bfc_launch_count() -> int:

@@ -59,11 +59,40 @@ void profile_end(const char *tag, cudaStream_t s) {
   e.open = nullptr;
 }
 
+// The library's own stream-ordered memory pool on each device, which keeps
+// the memory it is given back (release threshold: unlimited) so that the
+// next call's allocations reuse it instead of mapping new pages;
+// bfc_trim_memory hands it back.
+constexpr int MAX_DEVICES = 64;
+static cudaMemPool_t g_pools[MAX_DEVICES];
+static std::mutex g_pool_mu;
+static int lib_pool(cudaMemPool_t *pool) {
+  int dev = 0;
+  BFC_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= MAX_DEVICES) return BFC_EINTERNAL;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    BFC_CUDA_TRY(cudaMemPoolCreate(&p, &props));
+    uint64_t keep = ~0ull;
+    BFC_CUDA_TRY(cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep));
+    g_pools[dev] = p;
+  }
+  *pool = g_pools[dev];
+  return BFC_OK;
+}
+
 int dalloc(DBuf &b, size_t bytes, cudaStream_t s) {
   if (b.p && b.bytes >= bytes) return BFC_OK;
   dfree(b, s);
   if (bytes == 0) bytes = 16;
-  BFC_CUDA_TRY(cudaMallocAsync(&b.p, bytes, s));
+  cudaMemPool_t pool = nullptr;
+  BFC_TRY(lib_pool(&pool));
+  BFC_CUDA_TRY(cudaMallocFromPoolAsync(&b.p, bytes, pool, s));
   b.bytes = bytes;
   return BFC_OK;
 }
@@ -403,6 +432,16 @@ int radix_sort_u32(const uint32_t *keys_in, uint32_t *keys_out, const uint32_t *
 
 extern "C" {
 uint64_t bfc_launch_count(void) { return bfc::launches_total(); }
+
+int bfc_trim_memory(void) {
+  std::lock_guard<std::mutex> lk(bfc::g_pool_mu);
+  for (int d = 0; d < bfc::MAX_DEVICES; d++) {
+    if (!bfc::g_pools[d]) continue;
+    if (cudaDeviceSynchronize() != cudaSuccess) return BFC_ECUDA;
+    if (cudaMemPoolTrimTo(bfc::g_pools[d], 0) != cudaSuccess) return BFC_ECUDA;
+  }
+  return BFC_OK;
+}
 
 int bfc_profile_enable(int on) {
   bfc::g_prof_on = on != 0;
