@@ -173,9 +173,11 @@ int bfc_per_edge(bfc_graph *g, uint32_t flags, uint64_t *be, uint64_t *out_B, vo
 
 /* vBFC and eBFC together in one sweep (Algorithm 2's counts for every vertex
  * and the per-edge counts of Section 2).  Default: the ordered sweep of
- * Algorithm 1, where each pair {v, w} of start vertices with c = |Gamma_v ^
- * Gamma_w| adds C(c, 2) to b_v and b_w, and each wedge v - x - w adds c - 1
- * to b_x, b_(v,x) and b_(w,x).  BFC_WHOLE_ROWS: Algorithm 2 for every start
+ * Algorithm 1, where each wedge v - x - w of a pair {v, w} of start vertices
+ * with c = |Gamma_v ^ Gamma_w| adds c - 1 to b_(v,x) and b_(w,x); every
+ * vertex count then follows from b_y = 1/2 sum of b_e over y's edges (each
+ * butterfly through y holds two of y's edges).  bfc_per_vertex and
+ * bfc_per_edge run the same sweep.  BFC_WHOLE_ROWS: Algorithm 2 for every start
  * vertex v gives b_v and the row sums b_(v,x) = sum over w in Gamma_x \ {v}
  * of (c(v, w) - 1), and the midpoint side gets b_x = 1/2 sum of b_e over x's
  * edges.

@@ -303,11 +303,6 @@ struct Ctr {
     wi = idx - q * WIN_WORDS;
     sh = q * CW;
   }
-  __device__ static __forceinline__ void inc(uint32_t *c, uint32_t idx) {
-    uint32_t wi, sh;
-    at(idx, wi, sh);
-    atomicAdd(&c[wi], 1u << sh);
-  }
   // increment and return the field's old value
   __device__ static __forceinline__ uint32_t inc_get(uint32_t *c, uint32_t idx) {
     uint32_t wi, sh;
@@ -326,9 +321,9 @@ struct Ctr {
 // in-window ones are a prefix.  On return cur is the first target >= hi (or
 // end) and nx that target's rank (INF_RANK at the end of the segment).
 // Raising a counter from c to c + 1 adds exactly c new pairs (C(c+1, 2) -
-// C(c, 2) = c), so when ACC is set the old field values are summed into acc:
-// after the window acc holds sum_w C(c(v, w), 2) over its targets.
-template <int MODE, int CW, uint32_t WIN_WORDS, bool ACC>
+// C(c, 2) = c), so the old field values are summed into acc: after the
+// window acc holds sum_w C(c(v, w), 2) over its targets.
+template <int MODE, int CW, uint32_t WIN_WORDS>
 __device__ __forceinline__ void count_segment(const uint32_t *__restrict__ mR, uint32_t &cur, uint32_t end,
                                               uint32_t lo, uint32_t hi, uint32_t r, uint32_t *ctr, uint32_t &nx,
                                               uint64_t &acc) {
@@ -344,10 +339,7 @@ __device__ __forceinline__ void count_segment(const uint32_t *__restrict__ mR, u
     for (int k = 0; k < 4; k++) {
       const bool in = w[k] < hi;
       const uint32_t bal = __ballot_sync(0xffffffffu, in);
-      if (in && (!Full<MODE>::value || w[k] != r)) {
-        if (ACC) acc += Ctr<CW, WIN_WORDS>::inc_get(ctr, w[k] - lo);
-        else Ctr<CW, WIN_WORDS>::inc(ctr, w[k] - lo);
-      }
+      if (in && (!Full<MODE>::value || w[k] != r)) acc += Ctr<CW, WIN_WORDS>::inc_get(ctr, w[k] - lo);
       const uint32_t n = __popc(bal);
       cur += n;
       if (n < 32) {
@@ -380,7 +372,6 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win
   constexpr int NW = WIN_THREADS / 32;
   constexpr uint32_t Z = C::Z;
   // B accumulates at increment time (the sum of old values is C(c, 2))
-  constexpr bool ACC = true;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (uint32_t i = threadIdx.x; i < WIN_WORDS; i += WIN_THREADS) ctr[i] = 0;
   uint64_t localB = 0;
@@ -457,7 +448,7 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win
           const uint32_t sg = s0 + (uint32_t)l * NW;
           uint32_t cur = s_cur[sg], nx = INF_RANK;
           const uint32_t ps = cur;
-          count_segment<MODE, CW, WIN_WORDS, ACC>(a.mR, cur, s_end[sg], lo, hi, r, ctr, nx, acc);
+          count_segment<MODE, CW, WIN_WORDS>(a.mR, cur, s_end[sg], lo, hi, r, ctr, nx, acc);
           if (lane == 0) {
             s_cur[sg] = cur;
             s_nx[sg] = nx;
@@ -624,7 +615,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_big(WArgs a) {
           bal &= bal - 1;
           uint32_t *sg = seg + (size_t)(s0 + (uint32_t)l * NW) * 5;
           uint32_t pos = sg[2], nxt = INF_RANK;
-          count_segment<MODE, 32, BIG_Z, true>(a.mR, pos, sg[1], lo, hi, r, ctr, nxt, acc);
+          count_segment<MODE, 32, BIG_Z>(a.mR, pos, sg[1], lo, hi, r, ctr, nxt, acc);
           if (lane == 0) { sg[2] = pos; sg[4] = nxt; }
           if (lane == l) my_nx = nxt;
         }
