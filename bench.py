@@ -38,10 +38,10 @@ CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.a
 
 
 # DRAM bytes (read + write) per call of each counting-kernel set, from one ncu
-# capture of this workload (profiles/win_edge_chung_lu_1m_5m.md), valid only
+# capture of this workload (profiles/launches_chung_lu_1m_5m.md), valid only
 # for the kernel source they were taken with (its SHA-256 prefix).
-MEASURED_TRAFFIC = {"source_sha256": "05f8d735689b89d0",
-                    "bytes": {"win.edge": 17.055e9, "win.total": 5.703e9, "big.edge": 7.366e9}}
+MEASURED_TRAFFIC = {"source_sha256": "50aede1bc00e8ef0",
+                    "bytes": {"win.edge": 17.03e9, "win.total": 5.706e9, "big.edge": 7.364e9}}
 
 
 def measured_traffic(tag: str):
@@ -130,6 +130,11 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def AT_DEFAULT():
+    from paper_1801_00338_gb300 import autotune as AT
+    return dict(AT.DEFAULT)
 
 
 def workload():
@@ -238,6 +243,8 @@ def run_own(args, rank, world, local_rank):
     def step():
         h = bfc.bfc_graph_from_edges(du, dv, nU, nV, 0, sptr)
         try:
+            if tuning:
+                bfc.bfc_set_tuning(h, tuning)
             bfc._check(L.bfc_exact(h, bfc.BFC_HUB_MMA, ctypes.byref(Bh), ctypes.byref(side_h), sptr), "bfc_exact")
             bfc._check(L.bfc_local_counts(h, 0, bU.data_ptr(), bV.data_ptr(), be.data_ptr(), ctypes.byref(B2h), sptr),
                        "bfc_local_counts")
@@ -253,6 +260,23 @@ def run_own(args, rank, world, local_rank):
     assert Bhub == Bval
     st = G.stats
     W = st["wedges_v"] if side == 0 else st["wedges_u"]
+    # scheduling settings of the step's counting calls, chosen by the
+    # autotuner on this graph (not timed; every candidate's counts are checked
+    # equal); --no-autotune keeps the defaults
+    tuning, tune_info = None, {"source": "defaults"}
+    if not args.no_autotune:
+        from paper_1801_00338_gb300 import autotune as AT
+        res = AT.autotune(G, ("exact", "local"), use_cache=False)
+        assert res.counts[0] == Bval
+        tuning = res.tuning
+        tune_info = {"source": "autotuner (" + res.source + ")", "tuned_ms": res.ms, "default_ms": res.default_ms,
+                     "candidates_timed": len(res.tried)}
+        for t, ms in res.tried:
+            print(f"autotune {ms:9.3f} ms {t}", file=sys.stderr)
+    if tuning and tuning["hubs"] != bfc.BFC_TUNE_NO_HUBS:
+        # the hub block as the tuned step runs it (for its roofline below)
+        _, _, hub_stats = G.exact_hub(hubs=min(tuning["hubs"], (nV if side else nU) // 128 * 128),
+                                      tau=tuning["tau"])
     ps = G.plan_stats(side)
     G.close()
 
@@ -295,6 +319,8 @@ def run_own(args, rank, world, local_rank):
                    "bfc_graph_from_edges")
         h = hh.value
         try:
+            if tuning:
+                bfc.bfc_set_tuning(h, tuning)
             bfc._check(L.bfc_exact(h, bfc.BFC_HUB_MMA, ctypes.byref(Bh), ctypes.byref(side_h), sptr), "bfc_exact")
             bfc._check(L.bfc_local_counts(h, 0, bU.data_ptr(), bV.data_ptr(), be.data_ptr(), ctypes.byref(B2h), sptr),
                        "bfc_local_counts")
@@ -360,7 +386,8 @@ def run_own(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "nU": nU, "nV": nV, "m": m, "W": W, "B": Bval, "start_side": "UV"[side],
                    "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (edge list 400 MB)",
-                   "classes": ps["count"], "class_wedges": ps["work"]},
+                   "classes": ps["count"], "class_wedges": ps["work"],
+                   "tuning": dict(tuning or AT_DEFAULT(), **tune_info)},
         "e2e": {"value": whole_job_rate(world, W, e2e_ms), "unit": "wedges/s", "ms_per_step": e2e_ms,
                 "ms_per_step_min_max": [min(e2e_times), max(e2e_times)], "steps_timed": e2e_steps,
                 "h2d_bytes_per_step": 8 * m, "d2h_bytes_per_step": 8 * (nU + nV + m) + 16},
@@ -389,6 +416,7 @@ def main():
     ap.add_argument("--impl", choices=("own", "reference"), default="own")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="count with the default scheduling settings")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -341,6 +341,48 @@ int bfc_profile_enable(int on);
 int bfc_profile_reset(void);
 int bfc_profile_read(const char *tag, uint64_t *launches, double *total_ms);
 
+/* ---- scheduling settings (no counterpart in the paper) ------------------- */
+
+/* How one graph's counting work is scheduled on the GPU.  The settings never
+ * change a count, only its speed; they are picked per graph by the
+ * autotuner of the Python package (paper_1801_00338_gb300/autotune.py),
+ * which times the candidates and checks that their counts agree.  A field
+ * left 0 keeps the built-in default.
+ *   warp_max_wedges : start vertices that walk at most this many wedges
+ *                     (Lemma 3's per-vertex work) get one warp and a
+ *                     shared-memory hash table; 1..512, default 512 (the
+ *                     table's capacity at load factor 1/2).
+ *   small_max_segs  : the others whose wedge lists hold at most this many
+ *                     segments of 256 wedges (plus one per row) run in the
+ *                     512-thread window CTAs (three per SM, 64 KB counter
+ *                     windows); above it, up to 1,536 segments, in the
+ *                     1,024-thread CTAs (one per SM, 192 KB windows), and
+ *                     beyond that in the big-class kernel; 1..512, default 512.
+ *   hubs            : hub count of bfc_exact with BFC_HUB_MMA: 0 the automatic
+ *                     choice (bfc_exact_hub with hubs = 0), BFC_TUNE_NO_HUBS
+ *                     none (the walk counts every pair), else a multiple of
+ *                     128 <= BFC_HUB_MAX (capped at the start side's size).
+ *   tau             : that hub block's dense-column threshold (0: the cost
+ *                     model; else >= 2).
+ *   local_sweep     : the sweep of bfc_local_counts, bfc_per_vertex and
+ *                     bfc_per_edge when BFC_WHOLE_ROWS is not given: 0 the
+ *                     ordered sweep, 1 whole rows.
+ * A changed class limit redoes the cached classification of the start
+ * vertices on the next counting call (the rank layout is kept).
+ * Errors: BFC_EINVAL (null handle, a value out of range). */
+typedef struct bfc_tuning {
+  uint32_t warp_max_wedges;
+  uint32_t small_max_segs;
+  uint32_t hubs;
+  uint32_t tau;
+  uint32_t local_sweep;
+} bfc_tuning;
+#define BFC_TUNE_NO_HUBS 0xFFFFFFFFu
+/* t == NULL restores every default. */
+int bfc_set_tuning(bfc_graph *g, const bfc_tuning *t);
+/* The settings in effect, with the class-limit defaults filled in. */
+int bfc_get_tuning(const bfc_graph *g, bfc_tuning *t);
+
 /* ---- allocation-free exact count (the paper has no counterpart) --------- */
 
 /* Size of the library-resident scratch array used by bfc_exact_csr_noalloc:

@@ -31,17 +31,40 @@ def wedges_at_start_side(u, v, nU, nV) -> int:
     return int((mid * (mid - 1) / 2).sum())
 
 
-def run(count: int, seed: int, m_lo: float, m_hi: float, reps: int = 3) -> dict:
+def _make(args):
+    i, nU, nV, m, gamma = args
+    u, v = synth.chung_lu_bipartite(nU, nV, m, gamma, gamma, 100_000 + i)
+    return u, v, nU, nV, wedges_at_start_side(u, v, nU, nV)
+
+
+def _one_thread():
     import torch
-    t0 = time.perf_counter()
+    torch.set_num_threads(1)
+
+
+def generate(count: int, seed: int, m_lo: float, m_hi: float, workers: int = 0):
+    """The batch's graphs and W of each, generated by a pool of worker
+    processes (spawned, so that no worker inherits a CUDA context)."""
+    import multiprocessing as mp
+    import os
     params = synth.uneven_batch_params(count, seed, m_lo, m_hi)
-    graphs = []
-    for i, (nU, nV, m, gamma) in enumerate(params):
-        u, v = synth.chung_lu_bipartite(nU, nV, m, gamma, gamma, 100_000 + i)
-        graphs.append((u, v, nU, nV))
+    jobs = [(i, nU, nV, m, gamma) for i, (nU, nV, m, gamma) in enumerate(params)]
+    workers = workers or min(16, os.cpu_count() or 1)
+    if workers > 1:
+        with mp.get_context("spawn").Pool(workers, initializer=_one_thread) as pool:
+            out = pool.map(_make, jobs, chunksize=8)
+    else:
+        out = [_make(j) for j in jobs]
+    graphs = [o[:4] for o in out]
+    return graphs, int(sum(o[4] for o in out))
+
+
+def run(count: int, seed: int, m_lo: float, m_hi: float, reps: int = 3) -> dict:
+    t0 = time.perf_counter()
+    graphs, W = generate(count, seed, m_lo, m_hi)
     gen_s = time.perf_counter() - t0
+    import torch
     edges = int(sum(len(g[0]) for g in graphs))
-    W = sum(wedges_at_start_side(*g) for g in graphs)
     bfc.bfc_exact_batch(graphs)  # warm-up (allocator pool, library load)
     times = []
     for _ in range(reps):

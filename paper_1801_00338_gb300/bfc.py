@@ -30,6 +30,12 @@ BFC_SIDE_V = 0x20
 BFC_WHOLE_ROWS = 0x100
 BFC_HUB_MMA = 0x200
 BFC_HUB_MAX = 16384
+BFC_TUNE_NO_HUBS = 0xFFFFFFFF
+TUNING_FIELDS = ("warp_max_wedges", "small_max_segs", "hubs", "tau", "local_sweep")
+
+
+class bfc_tuning(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint32) for f in TUNING_FIELDS]
 
 _lib = None
 
@@ -83,6 +89,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     for name, args in sig.items():
         f = getattr(L, name)
         f.argtypes = args
+        f.restype = i32
+    for name in ("bfc_set_tuning", "bfc_get_tuning"):
+        f = getattr(L, name)
+        f.argtypes = [P, ctypes.POINTER(bfc_tuning)]
         f.restype = i32
     L.bfc_plan_stats.argtypes = [P, i32, P, P]
     L.bfc_plan_stats.restype = i32
@@ -206,6 +216,25 @@ def bfc_graph_from_csr(offU, nbrU, nU: int, offV, nbrV, nV: int, eidV=None, stre
                                      _dptr(eidV) if eidV is not None else None, nV, _stream_ptr(stream),
                                      ctypes.byref(h)), "bfc_graph_from_csr")
     return h.value
+
+
+def bfc_set_tuning(h: int, tuning: dict | None):
+    """Scheduling settings of a graph (bfc.h: bfc_tuning); None restores the
+    defaults, a missing key means 0 (the default)."""
+    if tuning is None:
+        _check(load().bfc_set_tuning(h, None), "bfc_set_tuning")
+        return
+    unknown = set(tuning) - set(TUNING_FIELDS)
+    if unknown:
+        raise ValueError(f"unknown tuning fields {sorted(unknown)}")
+    t = bfc_tuning(*[int(tuning.get(f, 0)) for f in TUNING_FIELDS])
+    _check(load().bfc_set_tuning(h, ctypes.byref(t)), "bfc_set_tuning")
+
+
+def bfc_get_tuning(h: int) -> dict:
+    t = bfc_tuning()
+    _check(load().bfc_get_tuning(h, ctypes.byref(t)), "bfc_get_tuning")
+    return {f: int(getattr(t, f)) for f in TUNING_FIELDS}
 
 
 def bfc_graph_free(h: int):
@@ -500,6 +529,12 @@ class Graph:
     def local_counts(self, side=None, whole_rows=False, stream=None):
         return bfc_local_counts(self.h, self.nU, self.nV, self.m, _SIDE[side] | (BFC_WHOLE_ROWS if whole_rows else 0),
                                 stream)
+
+    def set_tuning(self, tuning: dict | None):
+        bfc_set_tuning(self.h, tuning)
+
+    def tuning(self) -> dict:
+        return bfc_get_tuning(self.h)
 
     def plan_stats(self, side: int, stream=None):
         return bfc_plan_stats(self.h, side, stream)

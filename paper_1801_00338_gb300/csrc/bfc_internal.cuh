@@ -129,6 +129,9 @@ struct Plan {
   uint64_t cls_work[NCLS] = {};       // wedges walked per class
   uint64_t cls_rows[NCLS] = {};       // start-row entries per class
   uint32_t big_seg_cap = 0;           // segment capacity of the big class
+  // class limits the classification was made with (bfc_tuning's
+  // warp_max_wedges and small_max_segs; wedge.cu caps them)
+  uint32_t warp_max = 512, small_max = 512;
   uint64_t total_work = 0;     // sum of work = W of the midpoint side
   uint32_t max_deg_S = 0;
 };
@@ -148,6 +151,7 @@ struct bfc_graph {
   bfc::DBuf beM;               // u64[m]  per-edge partial sums in midpoint-row order
   bfc::DBuf err;               // u32 device error word
   bfc::DBuf acc;               // u64 accumulators (small)
+  bfc_tuning tune = {};        // scheduling settings (bfc_set_tuning; 0 = default)
   cudaStream_t last_stream = nullptr;
 };
 

@@ -153,7 +153,14 @@ int bfc_exact_hub(bfc_graph *g, uint32_t flags, uint32_t hubs, uint32_t tau, uin
 
 int bfc_exact(bfc_graph *g, uint32_t flags, uint64_t *out_B, int *out_side, void *stream) {
   if (!out_B) return BFC_EINVAL;
-  if (flags & BFC_HUB_MMA) return bfc_exact_hub(g, flags, 0, 0, out_B, out_side, nullptr, stream);
+  if (g && (flags & BFC_HUB_MMA) && g->tune.hubs != BFC_TUNE_NO_HUBS) {
+    // a tuned hub count is capped at the start side's size (whole tiles)
+    const uint32_t nS = choose_side(g, flags) ? g->nV : g->nU;
+    const uint32_t h = std::min<uint32_t>(g->tune.hubs, nS / 128 * 128);
+    if (g->tune.hubs == 0 || h > 0)
+      return bfc_exact_hub(g, flags, h, g->tune.tau, out_B, out_side, nullptr, stream);
+  }
+  flags &= ~BFC_HUB_MMA;
   cudaStream_t s = as_stream(stream);
   int side = 0;
   BFC_TRY(prepare(g, flags, s, &side));
@@ -209,10 +216,36 @@ static int ordered_local(bfc_graph *g, uint32_t flags, uint64_t *bU, uint64_t *b
   return rc;
 }
 
+// the sweep of the local counts: BFC_WHOLE_ROWS, or the graph's tuned default
+static uint32_t local_flags(const bfc_graph *g, uint32_t flags) {
+  return (g->tune.local_sweep == 1) ? (flags | BFC_WHOLE_ROWS) : flags;
+}
+
+int bfc_set_tuning(bfc_graph *g, const bfc_tuning *t) {
+  if (!g) return BFC_EINVAL;
+  if (!t) {
+    g->tune = bfc_tuning{};
+    return BFC_OK;
+  }
+  if (t->warp_max_wedges > 512 || t->small_max_segs > 512 || t->tau == 1 || t->local_sweep > 1) return BFC_EINVAL;
+  if (t->hubs != 0 && t->hubs != BFC_TUNE_NO_HUBS && (t->hubs % 128 || t->hubs > BFC_HUB_MAX)) return BFC_EINVAL;
+  g->tune = *t;
+  return BFC_OK;
+}
+
+int bfc_get_tuning(const bfc_graph *g, bfc_tuning *t) {
+  if (!g || !t) return BFC_EINVAL;
+  *t = g->tune;
+  if (!t->warp_max_wedges) t->warp_max_wedges = 512;
+  if (!t->small_max_segs) t->small_max_segs = 512;
+  return BFC_OK;
+}
+
 int bfc_local_counts(bfc_graph *g, uint32_t flags, uint64_t *bU, uint64_t *bV, uint64_t *be, uint64_t *out_B,
                      void *stream) {
   if (!g) return BFC_EINVAL;
   cudaStream_t s = as_stream(stream);
+  flags = local_flags(g, flags);
   if (flags & BFC_WHOLE_ROWS) return whole_rows(g, flags, bU, bV, be, out_B, s);
   return ordered_local(g, flags, bU, bV, be, out_B, s);
 }
@@ -220,6 +253,7 @@ int bfc_local_counts(bfc_graph *g, uint32_t flags, uint64_t *bU, uint64_t *bV, u
 int bfc_per_vertex(bfc_graph *g, uint32_t flags, uint64_t *bU, uint64_t *bV, uint64_t *out_B, void *stream) {
   if (!g) return BFC_EINVAL;
   cudaStream_t s = as_stream(stream);
+  flags = local_flags(g, flags);
   if (!(flags & BFC_WHOLE_ROWS)) return ordered_local(g, flags, bU, bV, nullptr, out_B, s);
   DBuf tU, tV;
   uint64_t *pU = bU, *pV = bV;
@@ -234,6 +268,7 @@ int bfc_per_vertex(bfc_graph *g, uint32_t flags, uint64_t *bU, uint64_t *bV, uin
 int bfc_per_edge(bfc_graph *g, uint32_t flags, uint64_t *be, uint64_t *out_B, void *stream) {
   if (!g || (!be && g->m > 0)) return BFC_EINVAL;
   cudaStream_t s = as_stream(stream);
+  flags = local_flags(g, flags);
   if (flags & BFC_WHOLE_ROWS) return whole_rows(g, flags, nullptr, nullptr, be, out_B, s);
   return ordered_local(g, flags, nullptr, nullptr, be, out_B, s);
 }

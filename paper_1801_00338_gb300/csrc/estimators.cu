@@ -148,6 +148,8 @@ static int pipe_init(bfc_graph *g, const Plan &parent, uint32_t trials, TrialPip
   out.nM = parent.nM;
   out.m = m;
   out.max_deg_S = parent.max_deg_S;
+  out.warp_max = parent.warp_max;
+  out.small_max = parent.small_max;
   out.vert_of = DBuf{parent.vert_of.p, 0};  // borrowed: bytes = 0 marks "not owned"
   out.rank_of = DBuf{parent.rank_of.p, 0};
   BFC_TRY(dalloc(out.offR, ((uint64_t)out.nS + 1) * 8, s));

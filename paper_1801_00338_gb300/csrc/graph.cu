@@ -412,9 +412,26 @@ __global__ void k_work(const uint64_t *offR, uint32_t nS, const uint32_t *sX, co
 
 int plan_classify(bfc_graph *g, Plan &p, cudaStream_t s);  // wedge.cu
 
+// class limits of the graph's tuning (0 = the default)
+static void tuned_limits(const bfc_graph *g, uint32_t *warp_max, uint32_t *small_max) {
+  *warp_max = g->tune.warp_max_wedges ? g->tune.warp_max_wedges : 512u;
+  *small_max = g->tune.small_max_segs ? g->tune.small_max_segs : 512u;
+}
+
 int plan_build(bfc_graph *g, int side, cudaStream_t s) {
   Plan &p = g->plan[side];
-  if (p.built) return BFC_OK;
+  uint32_t wmax, smax;
+  tuned_limits(g, &wmax, &smax);
+  if (p.built) {
+    if (p.warp_max == wmax && p.small_max == smax) return BFC_OK;
+    // the tuning changed a class limit: redo the classification only
+    dfree(p.cls, s);
+    p.warp_max = wmax;
+    p.small_max = smax;
+    return plan_classify(g, p, s);
+  }
+  p.warp_max = wmax;
+  p.small_max = smax;
   p.side = side;
   const uint32_t nS = side ? g->nV : g->nU, nM = side ? g->nU : g->nV;
   const uint64_t m = g->m;

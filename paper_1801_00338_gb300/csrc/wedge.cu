@@ -351,6 +351,39 @@ __device__ __forceinline__ void count_segment(const uint32_t *__restrict__ mR, u
   }
 }
 
+// Read sweep of one counted piece mR[ps, pe) of a wedge list (EDGE and
+// LOCAL modes), after the window's counts are final: the target w of entry i
+// has multiplicity c = peek(w - lo) = c(v, w), and the wedge v - x - w adds
+// c - 1 to the far edge (w, x) (EDGE: staged at beM[i]) and to the near edge
+// (v, x) (the returned warp sum, valid in lane 0).  Four 32-element loads in
+// flight per warp, as in the count sweep.
+template <int MODE, class Peek>
+__device__ __forceinline__ uint64_t read_piece(const uint32_t *__restrict__ mR, unsigned long long *beM, uint32_t ps,
+                                               uint32_t pe, uint32_t lo, Peek peek) {
+  const int lane = threadIdx.x & 31;
+  uint64_t rowsum = 0;
+  for (uint32_t i0 = ps; i0 < pe; i0 += 128) {
+    uint32_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const uint32_t i = i0 + k * 32 + lane;
+      w[k] = (i < pe) ? __ldg(&mR[i]) : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const uint32_t i = i0 + k * 32 + lane;
+      if (i < pe) {
+        const uint32_t c = peek(w[k] - lo);
+        if (c > 1) {
+          rowsum += c - 1;
+          if (MODE != MODE_LOCAL) atomicAdd(&beM[i], (unsigned long long)(c - 1));
+        }
+      }
+    }
+  }
+  return warp_sum_u64(rowsum);
+}
+
 template <int MODE, int CW, int P>
 __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win(WArgs a) {
   constexpr int WIN_THREADS = WinCfg<P>::THREADS;
@@ -486,16 +519,8 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win
               const int l = __ffs(bal) - 1;
               bal &= bal - 1;
               const uint32_t sg = s0 + (uint32_t)l * NW;
-              const uint32_t ps = s_ps[sg], pe = s_cur[sg];
-              uint64_t rowsum = 0;
-              for (uint32_t i = ps + lane; i < pe; i += 32) {
-                const uint32_t c = C::peek(ctr, __ldg(&a.mR[i]) - lo);
-                if (c > 1) {
-                  rowsum += c - 1;
-                  if (MODE != MODE_LOCAL) atomicAdd(&a.beM[i], (unsigned long long)(c - 1));
-                }
-              }
-              rowsum = warp_sum_u64(rowsum);
+              const uint64_t rowsum = read_piece<MODE>(a.mR, a.beM, s_ps[sg], s_cur[sg], lo,
+                                                        [&](uint32_t idx) { return C::peek(ctr, idx); });
               if (lane == 0 && rowsum) atomicAdd(&a.be[a.sEid[rb + s_row[sg]]], (unsigned long long)rowsum);
             }
           }
@@ -634,16 +659,8 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_big(WArgs a) {
             bal &= bal - 1;
             const uint32_t sidx = s0 + (uint32_t)l * NW;
             const uint32_t *sg = seg + (size_t)sidx * 5;
-            const uint32_t ps = sg[3], pe = sg[2];
-            uint64_t rowsum = 0;
-            for (uint32_t i = ps + lane; i < pe; i += 32) {
-              const uint32_t c = ctr[__ldg(&a.mR[i]) - lo];
-              if (c > 1) {
-                rowsum += c - 1;
-                if (MODE != MODE_LOCAL) atomicAdd(&a.beM[i], (unsigned long long)(c - 1));
-              }
-            }
-            rowsum = warp_sum_u64(rowsum);
+            const uint64_t rowsum = read_piece<MODE>(a.mR, a.beM, sg[3], sg[2], lo,
+                                                      [&](uint32_t idx) { return ctr[idx]; });
             if (lane == 0 && rowsum) atomicAdd(&a.be[a.sEid[seg_row[sidx]]], (unsigned long long)rowsum);
           }
         }
@@ -680,12 +697,23 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_big(WArgs a) {
 // ---------------------------------------------------------------------------
 // classification
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t class_of(uint64_t d, uint64_t w) {
+// Class limits of a plan (tunable, see bfc_set_tuning): start vertices with
+// at most warp_max wedges take the warp class, those with at most small_max
+// segments the small windows.  Both are capped by the tables' capacities.
+struct ClsLimits {
+  uint32_t warp_max, small_max;
+};
+static ClsLimits limits_of(const Plan &p) {
+  return ClsLimits{std::min<uint32_t>(p.warp_max, (uint32_t)WH_MAX_WORK),
+                   std::min<uint32_t>(std::max<uint32_t>(p.small_max, 1u), WinCfg<P_SMALL>::SMAX)};
+}
+
+__device__ __forceinline__ uint32_t class_of(uint64_t d, uint64_t w, ClsLimits lim) {
   if (d < 2 || w == 0) return CLS_SKIP;
-  if (w <= WH_MAX_WORK) return CLS_WARP;
+  if (w <= lim.warp_max) return CLS_WARP;
   const uint64_t segs = d + w / SEG + 1;
   uint32_t base;
-  if (segs <= WinCfg<P_SMALL>::SMAX) base = CLS_S0;
+  if (segs <= lim.small_max) base = CLS_S0;
   else if (segs <= WinCfg<P_LARGE>::SMAX) base = CLS_L0;
   else return CLS_BIG;
   // counter width: every c(v, w) <= degree of v
@@ -696,17 +724,36 @@ __device__ __forceinline__ uint32_t class_of(uint64_t d, uint64_t w) {
   return base + 4;
 }
 
-__global__ void k_classify(const uint64_t *offR, const uint64_t *work, uint32_t nS, uint32_t *cls_of,
+// Class of every start rank, with per-class vertex counts, wedge and row
+// sums gathered in shared memory first (one global atomic per block and
+// class instead of one per vertex on the same few words).
+__global__ void k_classify(const uint64_t *offR, const uint64_t *work, uint32_t nS, ClsLimits lim, uint32_t *cls_of,
                            unsigned int *counts, unsigned long long *maxseg, unsigned long long *sums) {
+  constexpr int N = Plan::NCLS;
+  __shared__ unsigned int s_cnt[N];
+  __shared__ unsigned long long s_sum[2 * N];
+  __shared__ unsigned long long s_max;
+  for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) {
+    if (i < N) s_cnt[i] = 0;
+    s_sum[i] = 0;
+  }
+  if (threadIdx.x == 0) s_max = 0;
+  __syncthreads();
   for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nS; r += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t d = offR[r + 1] - offR[r], w = work[r];
-    const uint32_t c = class_of(d, w);
+    const uint32_t c = class_of(d, w, lim);
     cls_of[r] = c;
-    atomicAdd(&counts[c], 1u);
-    if (w) atomicAdd(&sums[c], (unsigned long long)w);
-    if (d) atomicAdd(&sums[Plan::NCLS + c], (unsigned long long)d);
-    if (c == CLS_BIG) atomicMax(maxseg, (unsigned long long)(d + w / BIG_SEG + 1));
+    atomicAdd(&s_cnt[c], 1u);
+    if (w) atomicAdd(&s_sum[c], (unsigned long long)w);
+    if (d) atomicAdd(&s_sum[N + c], (unsigned long long)d);
+    if (c == CLS_BIG) atomicMax(&s_max, (unsigned long long)(d + w / BIG_SEG + 1));
   }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) {
+    if (i < N && s_cnt[i]) atomicAdd(&counts[i], s_cnt[i]);
+    if (s_sum[i]) atomicAdd(&sums[i], s_sum[i]);
+  }
+  if (threadIdx.x == 0 && s_max) atomicMax(maxseg, s_max);
 }
 __global__ void k_scatter_class(const uint32_t *cls_of, uint32_t nS, const unsigned int *begin, unsigned int *cursor,
                                 uint32_t *list) {
@@ -750,7 +797,7 @@ int plan_classify(bfc_graph *g, Plan &p, cudaStream_t s) {
   unsigned int *cursor = counts + 16;                                                 // [16, 32)
   unsigned long long *maxseg = reinterpret_cast<unsigned long long *>(counts + 32);  // 1
   unsigned long long *sums = reinterpret_cast<unsigned long long *>(counts + 34);    // 2 N (<= 32)
-  k_classify<<<grid_for(nS, 256), 256, 0, s>>>(ptr<uint64_t>(p.offR), ptr<uint64_t>(p.work), nS,
+  k_classify<<<grid_for(nS, 256), 256, 0, s>>>(ptr<uint64_t>(p.offR), ptr<uint64_t>(p.work), nS, limits_of(p),
                                               ptr<uint32_t>(cls_of), counts, maxseg, sums);
   count_launch();
   unsigned int hc[16];
@@ -926,7 +973,7 @@ static WArgs args_of(bfc_graph *g, Plan &p) {
 // batched Algorithm 2
 // ---------------------------------------------------------------------------
 __global__ void k_item_classify(const uint32_t *item_rank, uint32_t n, const uint64_t *offR, const uint32_t *sX,
-                                const uint64_t *offM, uint32_t *cls_of, unsigned int *counts,
+                                const uint64_t *offM, ClsLimits lim, uint32_t *cls_of, unsigned int *counts,
                                 unsigned long long *maxseg, unsigned long long *out) {
   const int lane = threadIdx.x & 31;
   uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -942,7 +989,7 @@ __global__ void k_item_classify(const uint32_t *item_rank, uint32_t n, const uin
     w = warp_sum_u64(w);
     if (lane == 0) {
       const uint64_t d = e - b;
-      const uint32_t c = class_of(d, w);
+      const uint32_t c = class_of(d, w, lim);
       cls_of[i] = c;
       atomicAdd(&counts[c], 1u);
       if (out) out[i] = 0;
@@ -981,7 +1028,7 @@ static int full_rows_batch(bfc_graph *g, Plan &p, int mode, const uint32_t *item
   unsigned int *cursor = counts + 32;                                                 // [32, 48)
   unsigned long long *maxseg = reinterpret_cast<unsigned long long *>(counts + 48);
   k_item_classify<<<grid_for((uint64_t)n_items * 32, 256), 256, 0, s>>>(item_rank, n_items, ptr<uint64_t>(p.offR),
-                                                                        ptr<uint32_t>(p.sX), p.offM,
+                                                                        ptr<uint32_t>(p.sX), p.offM, limits_of(p),
                                                                         ptr<uint32_t>(cls_of), counts, maxseg, out);
   count_launch();
   unsigned int hc[16];
@@ -1100,7 +1147,8 @@ __global__ void k_cls_offsets(unsigned int *dev) {
 
 int plan_classify_device(Plan &p, uint32_t *cls_of, unsigned int *dev, unsigned long long *sums, cudaStream_t s) {
   BFC_CUDA_TRY(cudaMemsetAsync(dev, 0, 48 * 4, s));
-  k_classify<<<grid_for(p.nS, 256), 256, 0, s>>>(ptr<uint64_t>(p.offR), ptr<uint64_t>(p.work), p.nS, cls_of, dev,
+  k_classify<<<grid_for(p.nS, 256), 256, 0, s>>>(ptr<uint64_t>(p.offR), ptr<uint64_t>(p.work), p.nS, limits_of(p),
+                                                cls_of, dev,
                                                 sums + 2 * Plan::NCLS, sums);
   count_launch();
   k_cls_offsets<<<1, 32, 0, s>>>(dev);
