@@ -64,6 +64,11 @@ __global__ void k_bt_orient(const uint32_t *u, const uint32_t *v, uint64_t m, co
     vv[e] = (uint32_t)(voff2[g] + (flip[g] ? a : x));
   }
 }
+// graph of every union U vertex (its graph's start side is the range uoff2[g] .. uoff2[g+1])
+__global__ void k_bt_group_of_vertex(uint32_t n, const uint64_t *uoff2, uint32_t G, uint32_t *grp) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    grp[i] = seg_of(uoff2, G, i);
+}
 __global__ void k_bt_group_of_rank(const uint32_t *vert_of, uint32_t nS, const uint64_t *uoff2, uint32_t G,
                                    uint32_t *grp) {
   for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nS; r += (uint64_t)gridDim.x * blockDim.x)
@@ -172,9 +177,18 @@ extern "C" int bfc_exact_batch(const uint32_t *u, const uint32_t *v, const uint6
                               BFC_INPUT_DEVICE, stream, &ug));
   dfree(uu, s);
   dfree(vv, s);
+  // rank the union's start vertices graph by graph (then by degree, id), so
+  // that a start vertex's later-ranked targets, all in its own graph, lie in
+  // one short rank range instead of being spread over the whole union
+  const uint32_t NS2 = (uint32_t)uoff2[G];
+  BT_TRY(dalloc(grp, (uint64_t)std::max<uint32_t>(NS2, 1) * 4, s));
+  k_bt_group_of_vertex<<<bt_grid(NS2, 256), 256, 0, s>>>(NS2, d_uoff2, G, ptr<uint32_t>(grp));
+  count_launch();
+  ug->rank_group = ptr<uint32_t>(grp);
+  ug->rank_group_max = G - 1;
   BT_TRY(plan_build(ug, 0, s));
+  ug->rank_group = nullptr;
   Plan &p = ug->plan[0];
-  BT_TRY(dalloc(grp, (uint64_t)std::max<uint32_t>(p.nS, 1) * 4, s));
   BT_TRY(dalloc(gB, (uint64_t)G * 8, s));
   BT_CUDA(cudaMemsetAsync(gB.p, 0, (uint64_t)G * 8, s));
   k_bt_group_of_rank<<<bt_grid(p.nS, 256), 256, 0, s>>>(ptr<uint32_t>(p.vert_of), p.nS, d_uoff2, G,

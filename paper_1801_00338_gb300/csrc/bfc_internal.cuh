@@ -152,6 +152,12 @@ struct bfc_graph {
   bfc::DBuf err;               // u32 device error word
   bfc::DBuf acc;               // u64 accumulators (small)
   bfc_tuning tune = {};        // scheduling settings (bfc_set_tuning; 0 = default)
+  // optional group of every U vertex (device, borrowed): the U-side plan then
+  // ranks by (group, degree, id), so each group's start vertices hold
+  // consecutive ranks and their wedge targets stay within them (a disjoint
+  // union of graphs, one group per graph)
+  const uint32_t *rank_group = nullptr;
+  uint32_t rank_group_max = 0;
   cudaStream_t last_stream = nullptr;
 };
 

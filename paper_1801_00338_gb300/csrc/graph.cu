@@ -362,6 +362,14 @@ __global__ void k_iota_and_copy(const uint32_t *deg, uint32_t n, uint32_t *keys,
     iota[i] = (uint32_t)i;
   }
 }
+__global__ void k_group_keys(const uint32_t *vert_of, const uint32_t *group, uint32_t n, uint32_t *keys,
+                             uint32_t *vals) {
+  for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t x = vert_of[r];
+    keys[r] = group[x];
+    vals[r] = x;
+  }
+}
 __global__ void k_rank_of(const uint32_t *vert_of, const uint32_t *deg, uint32_t n, uint32_t *rank_of, uint32_t *dR) {
   for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t x = vert_of[r];
@@ -468,6 +476,15 @@ int plan_build(bfc_graph *g, int side, cudaStream_t s) {
   count_launch();
   PB_TRY(radix_sort_u32(ptr<uint32_t>(k1), ptr<uint32_t>(k2), ptr<uint32_t>(i1), ptr<uint32_t>(p.vert_of), nS,
                         bits_for(p.max_deg_S), g->scr, s));
+  if (side == 0 && g->rank_group && nS > 0) {
+    // grouped ranks: a second stable sort by group gives the order (group,
+    // degree, id), so every group's start vertices hold consecutive ranks
+    k_group_keys<<<grid_for(nS, 256), 256, 0, s>>>(ptr<uint32_t>(p.vert_of), g->rank_group, nS, ptr<uint32_t>(k1),
+                                                   ptr<uint32_t>(i1));
+    count_launch();
+    PB_TRY(radix_sort_u32(ptr<uint32_t>(k1), ptr<uint32_t>(k2), ptr<uint32_t>(i1), ptr<uint32_t>(p.vert_of), nS,
+                          std::max(1, bits_for(g->rank_group_max)), g->scr, s));
+  }
   k_rank_of<<<grid_for(nS, 256), 256, 0, s>>>(ptr<uint32_t>(p.vert_of), degS, nS, ptr<uint32_t>(p.rank_of),
                                               ptr<uint32_t>(dR));
   count_launch();

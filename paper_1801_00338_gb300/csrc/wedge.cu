@@ -88,6 +88,11 @@ constexpr int CT_THREADS = 1024;
 constexpr uint32_t CT_WORDS = 48 * 1024;          // 192 KB of counter words
 constexpr uint32_t BIG_SEG = 256;
 constexpr uint32_t BIG_Z = CT_WORDS;
+// single-window vertices take the flat expansion (count_flat) only when their
+// wedge lists are short: at most this many targets per start-row entry on
+// average.  Longer lists keep the segment path, whose 256-wedge segments
+// spread a few long lists over every warp of the CTA.
+constexpr uint64_t FLAT_MAX_AVG = 64;
 
 struct WArgs {
   uint32_t nS;
@@ -96,6 +101,7 @@ struct WArgs {
   const uint64_t *offM;
   const uint32_t *mR, *mEid;
   const uint32_t *vert_of;
+  const uint64_t *work;  // wedges walked from each start rank (the ordered suffixes)
   const uint32_t *list;
   uint32_t list_n;
   unsigned int *queue;
@@ -384,6 +390,102 @@ __device__ __forceinline__ uint64_t read_piece(const uint32_t *__restrict__ mR, 
   return warp_sum_u64(rowsum);
 }
 
+// Expand the wedge lists of start-row entries [cb, ce) (at most 32, one per
+// lane) and call f(i, w, l) for every target index i (into mR), its target
+// w = mR[i] and its row cb + l.  The warp takes 32 consecutive elements of
+// the concatenated lists at a time (prefix sum of the lengths + shuffle
+// search), four of them in flight; each lane's row index never decreases.
+// All 32 lanes must call this together.  FULL: whole midpoint rows.
+template <bool FULL, class F>
+__device__ __forceinline__ void expand_rows(const WArgs &a, uint64_t cb, uint64_t ce, F f) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t j = cb + lane;
+  uint32_t b = 0, len = 0;
+  if (j < ce) {
+    const uint32_t x = a.sX[j];
+    b = FULL ? (uint32_t)a.offM[x] : a.sB[j];
+    len = (uint32_t)a.offM[x + 1] - b;
+  }
+  const uint32_t incl = warp_incl_scan_u32(len);
+  const uint32_t excl = incl - len;
+  const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
+  for (uint32_t base = 0; base < T; base += 128) {
+    uint32_t idx[4], w[4];
+    int row[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const uint32_t t = base + k * 32 + lane;
+      int l = 0;
+#pragma unroll
+      for (int step = 16; step >= 1; step >>= 1) {
+        const int c = l + step;
+        const uint32_t ex = __shfl_sync(0xffffffffu, excl, c);
+        if (ex <= t) l = c;
+      }
+      const uint32_t sb = __shfl_sync(0xffffffffu, b, l);
+      const uint32_t sx = __shfl_sync(0xffffffffu, excl, l);
+      idx[k] = (t < T) ? sb + (t - sx) : 0xFFFFFFFFu;
+      row[k] = l;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) w[k] = (idx[k] != 0xFFFFFFFFu) ? __ldg(&a.mR[idx[k]]) : 0u;
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+      if (idx[k] != 0xFFFFFFFFu) f(idx[k], w[k], row[k]);
+  }
+}
+
+// A start vertex whose later ranks (every rank, in the whole-row modes) fit in
+// one counter window: no segments and no window walk.  Each warp takes the
+// start-row entries in chunks of 32 and counts their targets by expand_rows,
+// so short wedge lists (the top-ranked vertices' suffixes hold a few targets
+// each) keep every lane busy.  EDGE / LOCAL: after a barrier the same
+// expansion reads the final counts; the near edge's sum is gathered per row in
+// rs (32 u64 per warp, shared memory) and the far edge's update staged at
+// beM[i], as in the windowed path.  inc(idx) increments a counter and returns
+// its old value, peek(idx) reads it.  Ends with a barrier; the caller clears
+// the counters and reduces acc.
+template <int MODE, int NW, class Inc, class Peek>
+__device__ __forceinline__ void count_flat(const WArgs &a, uint32_t r, uint64_t rb, uint64_t re, uint32_t lo,
+                                           unsigned long long *rs_all, uint64_t &acc, Inc inc, Peek peek) {
+  constexpr bool FULL = Full<MODE>::value;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t acc_before = acc;
+  for (uint64_t cb = rb + (uint64_t)warp * 32; cb < re; cb += (uint64_t)NW * 32)
+    expand_rows<FULL>(a, cb, umin64(cb + 32, re), [&](uint32_t, uint32_t w, int) {
+      if (!FULL || w != r) acc += inc(w - lo);
+    });
+  // the read sweep adds c - 1 > 0 only where some counter reached 2
+  const bool any2 = __syncthreads_or(acc != acc_before);
+  if ((MODE == MODE_EDGE || (MODE == MODE_LOCAL && a.be)) && any2) {
+    unsigned long long *rs = rs_all + warp * 32;
+    for (uint64_t cb = rb + (uint64_t)warp * 32; cb < re; cb += (uint64_t)NW * 32) {
+      rs[lane] = 0;
+      __syncwarp();
+      int cur = -1;
+      unsigned long long part = 0;
+      expand_rows<FULL>(a, cb, umin64(cb + 32, re), [&](uint32_t i, uint32_t w, int l) {
+        const uint32_t c = peek(w - lo);  // 0 for w = v itself (never incremented)
+        if (c > 1) {
+          if (l != cur) {
+            if (part) atomicAdd(&rs[cur], part);
+            cur = l;
+            part = 0;
+          }
+          part += c - 1;
+          if (MODE != MODE_LOCAL) atomicAdd(&a.beM[i], (unsigned long long)(c - 1));
+        }
+      });
+      if (part) atomicAdd(&rs[cur], part);
+      __syncwarp();
+      const uint64_t j = cb + lane;
+      if (j < re && rs[lane]) atomicAdd(&a.be[a.sEid[j]], rs[lane]);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
 template <int MODE, int CW, int P>
 __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win(WArgs a) {
   constexpr int WIN_THREADS = WinCfg<P>::THREADS;
@@ -423,6 +525,18 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win
     const uint32_t item = a.list[idx];
     const uint32_t r = (MODE == MODE_SINGLE) ? a.item_rank[item] : item;
     const uint64_t rb = a.offR[r], re = (r < a.rank_end) ? a.offR[r + 1] : rb;  // ranks >= rank_end: done elsewhere
+    const uint32_t lo0 = Full<MODE>::value ? 0u : r + 1;
+    uint64_t acc = 0;  // per thread, over the whole vertex
+    if ((uint64_t)a.nS <= (uint64_t)lo0 + Z && a.work[r] <= FLAT_MAX_AVG * (re - rb)) {
+      // ---- every later rank fits in one window and the lists are short:
+      // no segments, no window walk
+      count_flat<MODE, NW>(a, r, rb, re, lo0, reinterpret_cast<unsigned long long *>(s_cur), acc,
+                           [&](uint32_t i) { return C::inc_get(ctr, i); },
+                           [&](uint32_t i) { return C::peek(ctr, i); });
+      const uint32_t used = (uint32_t)umin64((uint64_t)WIN_WORDS, (uint64_t)a.nS - lo0);
+      uint4 *c4 = reinterpret_cast<uint4 *>(ctr);
+      for (uint32_t i = threadIdx.x; i < (used + 3) / 4; i += WIN_THREADS) c4[i] = make_uint4(0, 0, 0, 0);
+    } else {
     // ---- segments of the vertex's wedge lists
     for (uint64_t base = rb; base < re; base += WIN_THREADS) {
       const uint64_t j = base + threadIdx.x;
@@ -456,9 +570,8 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win
       __syncthreads();
     }
     const uint32_t nseg = min(sh_carry, WIN_SMAX);
-    uint32_t lo = Full<MODE>::value ? 0u : r + 1;
+    uint32_t lo = lo0;
     uint32_t hi = (uint32_t)umin64((uint64_t)a.nS, (uint64_t)lo + Z);
-    uint64_t acc = 0;  // per thread, over the whole vertex
     for (uint32_t par = 0;; par ^= 1) {
       // ---- count: warp w owns segments w, w + NW, ...; its lanes test 32 of them
       // at once and the whole warp counts each one that has targets below hi
@@ -539,6 +652,7 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win
       lo = nm;
       hi = (uint32_t)umin64((uint64_t)a.nS, (uint64_t)lo + Z);
     }
+    }
     acc = warp_sum_u64(acc);
     if (lane == 0 && acc) atomicAdd(&sh_acc, (unsigned long long)acc);
     __syncthreads();
@@ -560,7 +674,8 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win
 template <int MODE>
 __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_big(WArgs a) {
   resolve_list(a);
-  extern __shared__ uint32_t ctr[];  // BIG_Z counters
+  extern __shared__ uint32_t ctr[];  // BIG_Z counters, then 32 u64 per warp (count_flat's row sums)
+  unsigned long long *rs_all = reinterpret_cast<unsigned long long *>(ctr + BIG_Z);
   __shared__ uint32_t s_idx, s_next_min, s_carry;
   __shared__ unsigned long long s_acc;
   __shared__ uint32_t wtot[32];
@@ -584,6 +699,17 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_big(WArgs a) {
     const uint32_t item = a.list[idx];
     const uint32_t r = (MODE == MODE_SINGLE) ? a.item_rank[item] : item;
     const uint64_t rb = a.offR[r], re = (r < a.rank_end) ? a.offR[r + 1] : rb;  // ranks >= rank_end: done elsewhere
+    const uint32_t lo0 = Full<MODE>::value ? 0u : r + 1;
+    uint64_t acc = 0;  // per thread: sum of old counter values = sum C(c, 2)
+    if ((uint64_t)a.nS <= (uint64_t)lo0 + BIG_Z && a.work[r] <= FLAT_MAX_AVG * (re - rb)) {
+      // ---- every later rank fits in one window and the lists are short:
+      // no segments, no window walk
+      count_flat<MODE, NW>(a, r, rb, re, lo0, rs_all, acc, [&](uint32_t i) { return atomicAdd(&ctr[i], 1u); },
+                           [&](uint32_t i) { return ctr[i]; });
+      const uint32_t used = (uint32_t)umin64((uint64_t)BIG_Z, (uint64_t)a.nS - lo0);
+      uint4 *c4 = reinterpret_cast<uint4 *>(ctr);
+      for (uint32_t i = threadIdx.x; i < (used + 3) / 4; i += CT_THREADS) c4[i] = make_uint4(0, 0, 0, 0);
+    } else {
     for (uint64_t base = rb; base < re; base += CT_THREADS) {
       uint64_t j = base + threadIdx.x;
       uint32_t b = 0, e = 0, ns = 0;
@@ -617,9 +743,8 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_big(WArgs a) {
       __syncthreads();
     }
     const uint32_t nseg = min(s_carry, a.seg_cap);
-    uint32_t lo = Full<MODE>::value ? 0u : r + 1;
+    uint32_t lo = lo0;
     uint32_t hi = (uint32_t)umin64((uint64_t)a.nS, (uint64_t)lo + BIG_Z);
-    uint64_t acc = 0;  // per thread: sum of old counter values = sum C(c, 2)
     while (true) {
       // ---- count: warp w owns segments w, w + NW, ...; 32 tested per ballot
       uint32_t wmin = INF_RANK;
@@ -679,6 +804,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_big(WArgs a) {
       lo = nm;
       hi = (uint32_t)umin64((uint64_t)a.nS, (uint64_t)lo + BIG_Z);
       __syncthreads();
+    }
     }
     acc = warp_sum_u64(acc);
     if (lane == 0 && acc) atomicAdd(&s_acc, (unsigned long long)acc);
@@ -929,7 +1055,7 @@ static int launch_lists(bfc_graph *g, WArgs a, const uint32_t *const *lists, con
   if (have(CLS_BIG) && big_cap > 0) {
     WArgs c = a;
     setup(c, CLS_BIG);
-    const size_t smem = (size_t)BIG_Z * 4;
+    const size_t smem = (size_t)BIG_Z * 4 + (size_t)CT_THREADS * 8;  // counters + per-warp row sums
     BFC_CUDA_TRY(cudaFuncSetAttribute(k_cta_big<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const unsigned grid = cap((unsigned)sms, CLS_BIG);
     c.seg_cap = big_cap;
@@ -965,6 +1091,7 @@ static WArgs args_of(bfc_graph *g, Plan &p) {
   a.mR = ptr<uint32_t>(p.mR);
   a.mEid = ptr<uint32_t>(p.mEid);
   a.vert_of = ptr<uint32_t>(p.vert_of);
+  a.work = ptr<uint64_t>(p.work);
   a.err = ptr<uint32_t>(g->err);
   return a;
 }

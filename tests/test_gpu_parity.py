@@ -262,6 +262,20 @@ def test_batched_uneven_graphs_match_oracle(bfc):
         assert int(b) == ob and int(sd) == os_
 
 
+def test_batched_graphs_spanning_rank_windows(bfc):
+    """Graphs large enough that a start vertex's targets would span several
+    counter windows of the union, each counted within its own rank range."""
+    params = synth.uneven_batch_params(96, 23, m_lo=2_000, m_hi=200_000)
+    graphs = []
+    for i, (nU, nV, m, gamma) in enumerate(params):
+        u, v = synth.chung_lu_bipartite(nU, nV, m, gamma, gamma, 900 + i)
+        graphs.append((u, v, nU, nV))
+    B, side = bfc.bfc_exact_batch(graphs)
+    for (u, v, nU, nV), b, sd in zip(graphs, B, side):
+        ob, os_ = O.exact(u, v, nU, nV)
+        assert int(b) == ob and int(sd) == os_
+
+
 def _rows(u, v, nU, nV):
     """Host CSR of both sides: U rows ascending in v (canonical order), V rows
     ascending in u, and the canonical id of each V-row entry."""
