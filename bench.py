@@ -40,8 +40,8 @@ CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.a
 # DRAM bytes (read + write) per call of each counting-kernel set, from one ncu
 # capture of this workload (profiles/launches_chung_lu_1m_5m.md), valid only
 # for the kernel source they were taken with (its SHA-256 prefix).
-MEASURED_TRAFFIC = {"source_sha256": "7b2d5b14246b8df3",
-                    "bytes": {"win.edge": 17.04e9, "win.total": 5.71e9, "big.edge": 6.745e9}}
+MEASURED_TRAFFIC = {"source_sha256": "4d5f8ccd36b19316",
+                    "bytes": {"win.edge": 17.04e9, "win.total": 5.709e9, "big.edge": 6.753e9}}
 
 
 def measured_traffic(tag: str):

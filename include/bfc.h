@@ -367,6 +367,11 @@ int bfc_profile_read(const char *tag, uint64_t *launches, double *total_ms);
  *   local_sweep     : the sweep of bfc_local_counts, bfc_per_vertex and
  *                     bfc_per_edge when BFC_WHOLE_ROWS is not given: 0 the
  *                     ordered sweep, 1 whole rows.
+ *   flat_max_avg    : a window-class start vertex whose later ranks all fit in
+ *                     one counter window skips the window walk and expands its
+ *                     wedge lists 32 targets at a time when they hold at most
+ *                     this many targets per start-row entry on average;
+ *                     default 64, BFC_TUNE_NO_FLAT never.
  * A changed class limit redoes the cached classification of the start
  * vertices on the next counting call (the rank layout is kept).
  * Errors: BFC_EINVAL (null handle, a value out of range). */
@@ -376,8 +381,10 @@ typedef struct bfc_tuning {
   uint32_t hubs;
   uint32_t tau;
   uint32_t local_sweep;
+  uint32_t flat_max_avg;
 } bfc_tuning;
 #define BFC_TUNE_NO_HUBS 0xFFFFFFFFu
+#define BFC_TUNE_NO_FLAT 0xFFFFFFFFu
 /* t == NULL restores every default. */
 int bfc_set_tuning(bfc_graph *g, const bfc_tuning *t);
 /* The settings in effect, with the class-limit defaults filled in. */

@@ -4,9 +4,10 @@ The settings decide how the start vertices of Algorithm 1 are spread over the
 kernels: which vertices get a warp with a shared-memory hash table and which
 get a CTA with dense counter windows (the bucket thresholds), how many
 top-ranked vertices go to the tensor-core hub block and at which column
-density (the hash / window / MMA choice), and which sweep gives the local
-counts.  None of them changes a count (Lemma 1 sums over start vertices, in
-any grouping), only the time.
+density (the hash / window / MMA choice), which single-window vertices skip
+the window walk, and which sweep gives the local counts.  None of them
+changes a count (Lemma 1 sums over start vertices, in any grouping), only the
+time.
 
 For one graph, `autotune` times candidate settings of a workload of counting
 calls by coordinate descent (one setting at a time, the others fixed, a few
@@ -30,7 +31,8 @@ from dataclasses import dataclass, field
 from . import bfc
 
 NO_HUBS = bfc.BFC_TUNE_NO_HUBS
-DEFAULT = {"warp_max_wedges": 512, "small_max_segs": 512, "hubs": 0, "tau": 0, "local_sweep": 0}
+NO_FLAT = bfc.BFC_TUNE_NO_FLAT
+DEFAULT = {"warp_max_wedges": 512, "small_max_segs": 512, "hubs": 0, "tau": 0, "local_sweep": 0, "flat_max_avg": 64}
 # log-space distance under which another graph's cached choice is a starting point
 NEAR = 0.25
 
@@ -86,6 +88,8 @@ def candidates(knob: str, base: dict, info: dict) -> list[int]:
         return [512, 256, 128]
     if knob == "local_sweep":
         return [0, 1]
+    if knob == "flat_max_avg":
+        return [64, NO_FLAT, 16, 32, 128, 256]
     raise ValueError(knob)
 
 
@@ -94,7 +98,7 @@ def knobs_for(ops) -> list[str]:
     ks = []
     if "exact" in ops:
         ks += ["hubs", "tau"]
-    ks += ["small_max_segs", "warp_max_wedges"]
+    ks += ["small_max_segs", "warp_max_wedges", "flat_max_avg"]
     if "local" in ops:
         ks += ["local_sweep"]
     return ks

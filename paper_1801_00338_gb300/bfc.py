@@ -31,7 +31,8 @@ BFC_WHOLE_ROWS = 0x100
 BFC_HUB_MMA = 0x200
 BFC_HUB_MAX = 16384
 BFC_TUNE_NO_HUBS = 0xFFFFFFFF
-TUNING_FIELDS = ("warp_max_wedges", "small_max_segs", "hubs", "tau", "local_sweep")
+BFC_TUNE_NO_FLAT = 0xFFFFFFFF
+TUNING_FIELDS = ("warp_max_wedges", "small_max_segs", "hubs", "tau", "local_sweep", "flat_max_avg")
 
 
 class bfc_tuning(ctypes.Structure):

@@ -238,6 +238,7 @@ int bfc_get_tuning(const bfc_graph *g, bfc_tuning *t) {
   *t = g->tune;
   if (!t->warp_max_wedges) t->warp_max_wedges = 512;
   if (!t->small_max_segs) t->small_max_segs = 512;
+  if (!t->flat_max_avg) t->flat_max_avg = 64;
   return BFC_OK;
 }
 

@@ -89,10 +89,11 @@ constexpr uint32_t CT_WORDS = 48 * 1024;          // 192 KB of counter words
 constexpr uint32_t BIG_SEG = 256;
 constexpr uint32_t BIG_Z = CT_WORDS;
 // single-window vertices take the flat expansion (count_flat) only when their
-// wedge lists are short: at most this many targets per start-row entry on
-// average.  Longer lists keep the segment path, whose 256-wedge segments
-// spread a few long lists over every warp of the CTA.
-constexpr uint64_t FLAT_MAX_AVG = 64;
+// wedge lists are short: by default at most this many targets per start-row
+// entry on average (bfc_tuning.flat_max_avg).  Longer lists keep the segment
+// path, whose 256-wedge segments spread a few long lists over every warp of
+// the CTA.
+constexpr uint32_t FLAT_MAX_AVG = 64;
 
 struct WArgs {
   uint32_t nS;
@@ -102,6 +103,7 @@ struct WArgs {
   const uint32_t *mR, *mEid;
   const uint32_t *vert_of;
   const uint64_t *work;  // wedges walked from each start rank (the ordered suffixes)
+  uint32_t flat_max;     // flat expansion limit (targets per start-row entry), BFC_TUNE_NO_FLAT: never
   const uint32_t *list;
   uint32_t list_n;
   unsigned int *queue;
@@ -527,7 +529,8 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win
     const uint64_t rb = a.offR[r], re = (r < a.rank_end) ? a.offR[r + 1] : rb;  // ranks >= rank_end: done elsewhere
     const uint32_t lo0 = Full<MODE>::value ? 0u : r + 1;
     uint64_t acc = 0;  // per thread, over the whole vertex
-    if ((uint64_t)a.nS <= (uint64_t)lo0 + Z && a.work[r] <= FLAT_MAX_AVG * (re - rb)) {
+    if ((uint64_t)a.nS <= (uint64_t)lo0 + Z && a.flat_max != BFC_TUNE_NO_FLAT &&
+        a.work[r] <= (uint64_t)a.flat_max * (re - rb)) {
       // ---- every later rank fits in one window and the lists are short:
       // no segments, no window walk
       count_flat<MODE, NW>(a, r, rb, re, lo0, reinterpret_cast<unsigned long long *>(s_cur), acc,
@@ -701,7 +704,8 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_big(WArgs a) {
     const uint64_t rb = a.offR[r], re = (r < a.rank_end) ? a.offR[r + 1] : rb;  // ranks >= rank_end: done elsewhere
     const uint32_t lo0 = Full<MODE>::value ? 0u : r + 1;
     uint64_t acc = 0;  // per thread: sum of old counter values = sum C(c, 2)
-    if ((uint64_t)a.nS <= (uint64_t)lo0 + BIG_Z && a.work[r] <= FLAT_MAX_AVG * (re - rb)) {
+    if ((uint64_t)a.nS <= (uint64_t)lo0 + BIG_Z && a.flat_max != BFC_TUNE_NO_FLAT &&
+        a.work[r] <= (uint64_t)a.flat_max * (re - rb)) {
       // ---- every later rank fits in one window and the lists are short:
       // no segments, no window walk
       count_flat<MODE, NW>(a, r, rb, re, lo0, rs_all, acc, [&](uint32_t i) { return atomicAdd(&ctr[i], 1u); },
@@ -1092,6 +1096,7 @@ static WArgs args_of(bfc_graph *g, Plan &p) {
   a.mEid = ptr<uint32_t>(p.mEid);
   a.vert_of = ptr<uint32_t>(p.vert_of);
   a.work = ptr<uint64_t>(p.work);
+  a.flat_max = g->tune.flat_max_avg ? g->tune.flat_max_avg : FLAT_MAX_AVG;
   a.err = ptr<uint32_t>(g->err);
   return a;
 }

@@ -10,10 +10,12 @@ from paper_1801_00338_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 NO_HUBS = 0xFFFFFFFF
+NO_FLAT = 0xFFFFFFFF
 # extreme and typical settings: every vertex past the warp class in the large
 # windows or the big class (small_max_segs = 1), almost no warp class
 # (warp_max_wedges = 1), hub blocks of one tile and of none, the densest
-# column threshold, and whole-row local counts
+# column threshold, whole-row local counts, and the flat expansion of
+# single-window vertices never or always taken
 TUNINGS = [
     {},
     {"small_max_segs": 1},
@@ -23,6 +25,9 @@ TUNINGS = [
     {"hubs": 1024},
     {"hubs": NO_HUBS},
     {"local_sweep": 1, "small_max_segs": 200},
+    {"flat_max_avg": NO_FLAT},
+    {"flat_max_avg": 0xFFFFFFFE},
+    {"flat_max_avg": 0xFFFFFFFE, "local_sweep": 1},
 ]
 
 
