@@ -40,7 +40,7 @@ CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.a
 # DRAM bytes (read + write) per call of each counting-kernel set, from one ncu
 # capture of this workload (profiles/launches_chung_lu_1m_5m.md), valid only
 # for the kernel source they were taken with (its SHA-256 prefix).
-MEASURED_TRAFFIC = {"source_sha256": "4d5f8ccd36b19316",
+MEASURED_TRAFFIC = {"source_sha256": "0340c575e944ff8e",
                     "bytes": {"win.edge": 17.04e9, "win.total": 5.709e9, "big.edge": 6.753e9}}
 
 

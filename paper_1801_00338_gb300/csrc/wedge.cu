@@ -11,26 +11,32 @@
 // vBFC costs O(|Gamma^2_v|)) and by their degree (which bounds every c(v, w)):
 //   skip   degree < 2 or nothing after it: every c <= 1, contributes 0
 //   warp   <= 512 wedges: one warp per vertex, open addressing in shared memory
-//   win2   degree <= 3: one CTA per vertex, dense 2-bit counters in shared
-//          memory over a window of 786,432 consecutive ranks
-//   win4   degree <= 15: 4-bit counters (393,216 ranks)
-//   win8   degree <= 255: 8-bit counters (196,608 ranks)
-//   win16  degree <= 65,535: 16-bit counters (98,304 ranks)
-//   win32  32-bit counters (49,152 ranks)
-// Ranks ascend with degree, so the low-rank vertices, which walk the most of
-// the rank space, are exactly the ones with the narrowest counters and the
-// widest windows.
-//   big    more wedge-list segments than shared memory holds: the window kernel
-//          with its segment cursors in global memory
+//   small windows (<= 512 wedge-list segments of 256 targets): a 512-thread
+//          CTA (three per SM) with 16,384 counter words in shared memory
+//   large windows (<= 1,536 segments): a 1,024-thread CTA with 49,152 words
+//   big    more segments: the large CTA with its segment cursors in global
+//          memory and a 32-bit window
+// The window classes pack their counters by degree: 2 bits for degree <= 3,
+// 4 for <= 15, 8 for <= 255, 16 for <= 65,535, else 32, so a 16,384-word
+// window spans 262,144 ranks at 2 bits and 16,384 at 32.  Ranks ascend with
+// degree, so the low-rank vertices, which walk the most of the rank space,
+// are exactly the ones with the narrowest counters and the widest windows.
+// The thresholds are scheduling settings (bfc_tuning); the counts do not
+// depend on them.
+//
 // A window kernel walks the ranks after r window by window; a window starts at
 // the lowest rank still pending in any of the vertex's (rank-sorted) wedge
 // lists, so empty rank ranges cost nothing.  Each window has a count sweep
-// (shared-memory atomic increments whose old values sum to sum_w C(c, 2)) and
-// a clear of the counter words; VERTEX mode instead re-walks the window's
-// wedges, taking each distinct target's final count once as it clears it.
+// (shared-memory atomic increments whose old values sum to sum_w C(c, 2)), in
+// EDGE and LOCAL modes a read sweep of the same pieces against the final
+// counts, and a clear of the counter words.  A vertex whose later ranks all
+// fit in one window and whose lists are short skips the walk and expands its
+// lists 32 targets at a time (count_flat).
 //
-// Modes: TOTAL (B only), VERTEX (b for both sides), EDGE (b_e), SINGLE
-// (Algorithm 2 on a batch of vertices: every w != v, whole midpoint rows).
+// Modes: TOTAL (B only), EDGE (b_e; the vertex counts follow from b_e),
+// SINGLE (Algorithm 2 on a batch of vertices: every w != v, whole midpoint
+// rows), LOCAL (Algorithm 2 for every start vertex, with the row sums b_e).
+// Per wedge v - x - w of a pair with c = c(v, w):
 //   start side  b_v += sum_w C(c(v,w), 2), b_w += C(c(v,w), 2)
 //   mid side    b_x += c(v,w) - 1 for each wedge v - x - w (pairs through x)
 //   edges       b_(v,x) += c(v,w) - 1, b_(w,x) += c(v,w) - 1 for each wedge v - x - w
