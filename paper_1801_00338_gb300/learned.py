@@ -81,6 +81,34 @@ def dataset_from_graphs(graphs) -> Dataset:
     return Dataset(torch.cat(Xs), torch.cat(Ts), sizes)
 
 
+def save_checkpoint(path: str, state: dict):
+    """Write a training state (see Trainer.state) to an .npz file: the fp32
+    master weights, both Adam moments, the step count, the learning rate, the
+    mini-batch generator's state and any extra arrays (e.g. the training
+    graphs' parameters), so that training resumes exactly where it stopped."""
+    import json
+    arrays = {k: np.asarray(v) for k, v in state.items() if k != "rng"}
+    arrays["rng_json"] = np.array(json.dumps(state.get("rng")))
+    np.savez(path, **arrays)
+
+
+def load_checkpoint(path: str) -> dict:
+    import json
+    with np.load(path, allow_pickle=False) as z:
+        st = {k: z[k] for k in z.files if k != "rng_json"}
+        st["rng"] = json.loads(str(z["rng_json"]))
+    st["step"] = int(st["step"])
+    st["lr"] = float(st["lr"])
+    return st
+
+
+def rng_from_state(state) -> np.random.Generator:
+    """A PCG64 generator positioned at a saved bit-generator state."""
+    rng = np.random.default_rng()
+    rng.bit_generator.state = state
+    return rng
+
+
 class Trainer:
     """Adam on the fp32 master weights; the bf16 copy feeds the kernels."""
 
@@ -93,11 +121,33 @@ class Trainer:
         self.lr = lr
         self.step = 0
         self.history = []
+        self.rng = None  # mini-batch generator, seeded by the first fit()
+
+    def state(self, **extra) -> dict:
+        """The training state as host arrays (for save_checkpoint)."""
+        st = {"w": self.w.cpu().numpy(), "m": self.m.cpu().numpy(), "v": self.v.cpu().numpy(), "step": self.step,
+              "lr": self.lr, "rng": self.rng.bit_generator.state if self.rng is not None else None}
+        st.update(extra)
+        return st
+
+    def load_state(self, st: dict):
+        """Resume from a state written by save_checkpoint: weights, Adam
+        moments, step count and the mini-batch generator's position."""
+        import torch
+        self.w = torch.from_numpy(np.asarray(st["w"], np.float32)).cuda()
+        self.m = torch.from_numpy(np.asarray(st["m"], np.float32)).cuda()
+        self.v = torch.from_numpy(np.asarray(st["v"], np.float32)).cuda()
+        self.wb = bfc.bfc_mlp_to_bf16(self.w)
+        self.step = int(st["step"])
+        self.lr = float(st["lr"])
+        self.rng = rng_from_state(st["rng"]) if st.get("rng") is not None else None
 
     def fit(self, data: Dataset, steps: int, batch: int = 65536, seed: int = 1, log_every: int = 50):
         import torch
         n = data.X.shape[0]
-        rng = np.random.default_rng(seed)
+        if self.rng is None:
+            self.rng = np.random.default_rng(seed)
+        rng = self.rng
         for s in range(steps):
             idx = torch.from_numpy(rng.integers(0, n, min(batch, n), dtype=np.int64).astype(np.int32)).cuda()
             grad, loss = bfc.bfc_mlp_grad(self.wb, data.X, data.T, idx)

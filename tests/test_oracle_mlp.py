@@ -71,3 +71,4 @@ def test_features_from_definition_on_a_small_graph():
     # V vertex 1: degree 3, neighbours U0 (2), U1 (1), U2 (3)
     assert f[4, 1] == pytest.approx(math.log1p(6) / 16)
     assert f[4, 5] == pytest.approx(math.log1p(3) / 16)
+
