@@ -329,6 +329,14 @@ int bfc_plan_stats(bfc_graph *g, int side, uint64_t *out, void *stream);
  * memory.  Errors: BFC_ECUDA. */
 int bfc_trim_memory(void);
 
+/* Fault injection for tests of the error paths: after n more device
+ * allocations by the library succeed, the next one fails and its call
+ * returns BFC_ENOMEM, as a real out-of-memory would; the injection then
+ * switches itself off.  n < 0 switches it off.  Process-wide; an allocation
+ * that reuses a buffer already large enough does not count.  Every call is
+ * expected to leave its handles usable after such a failure. */
+int bfc_fail_alloc_after(int64_t n);
+
 /* Device timing of the library's counting kernels: when enabled, every
  * wedge-kernel launch is bracketed by CUDA events on the launch stream.
  * bfc_profile_read synchronises on the recorded events and returns, for the

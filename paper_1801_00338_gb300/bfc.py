@@ -95,6 +95,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         f = getattr(L, name)
         f.argtypes = [P, ctypes.POINTER(bfc_tuning)]
         f.restype = i32
+    L.bfc_fail_alloc_after.argtypes = [ctypes.c_int64]
+    L.bfc_fail_alloc_after.restype = i32
     L.bfc_plan_stats.argtypes = [P, i32, P, P]
     L.bfc_plan_stats.restype = i32
     L.bfc_profile_enable.argtypes = [i32]
@@ -137,6 +139,11 @@ def _stream_ptr(stream) -> int | None:
 
 def _dptr(t) -> int:
     return t.data_ptr()
+
+
+def bfc_fail_alloc_after(n: int):
+    """Make the library's (n+1)-th next device allocation fail (n < 0: none)."""
+    _check(load().bfc_fail_alloc_after(int(n)), "bfc_fail_alloc_after")
 
 
 def bfc_trim_memory():

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <map>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <utility>
@@ -86,13 +87,26 @@ static int lib_pool(cudaMemPool_t *pool) {
   return BFC_OK;
 }
 
+// Injected allocation failure (bfc_fail_alloc_after): the number of device
+// allocations that still succeed before one fails; negative: none fails.
+static std::atomic<long long> g_fail_after{-1};
+
 int dalloc(DBuf &b, size_t bytes, cudaStream_t s) {
   if (b.p && b.bytes >= bytes) return BFC_OK;
+  for (long long f = g_fail_after.load(); f >= 0;) {
+    if (f == 0) {
+      if (g_fail_after.compare_exchange_weak(f, -1)) return BFC_ENOMEM;
+    } else if (g_fail_after.compare_exchange_weak(f, f - 1)) {
+      break;
+    }
+  }
   dfree(b, s);
   if (bytes == 0) bytes = 16;
   cudaMemPool_t pool = nullptr;
   BFC_TRY(lib_pool(&pool));
-  BFC_CUDA_TRY(cudaMallocFromPoolAsync(&b.p, bytes, pool, s));
+  void *p = nullptr;  // b stays empty if the allocation fails
+  BFC_CUDA_TRY(cudaMallocFromPoolAsync(&p, bytes, pool, s));
+  b.p = p;
   b.bytes = bytes;
   return BFC_OK;
 }
@@ -432,6 +446,11 @@ int radix_sort_u32(const uint32_t *keys_in, uint32_t *keys_out, const uint32_t *
 
 extern "C" {
 uint64_t bfc_launch_count(void) { return bfc::launches_total(); }
+
+int bfc_fail_alloc_after(int64_t n) {
+  bfc::g_fail_after.store(n < 0 ? -1 : (long long)n);
+  return BFC_OK;
+}
 
 int bfc_trim_memory(void) {
   std::lock_guard<std::mutex> lk(bfc::g_pool_mu);
