@@ -53,3 +53,25 @@ def test_single_process_and_reference_arm_off_rank_0():
     class Args:
         steps, warmup = 1, 3
     assert bench.run_reference(Args(), rank=1, world=2) == 0   # no work, no line
+
+
+def test_all_cores_oracle_timing_counts_every_sampled_vertex():
+    """The all-cores CPU baseline deals the sampled start vertices to spawned
+    processes; with time to finish, their 2-paths add up to the single-process
+    walk over all vertices (the oracle's own count of the same loops)."""
+    import numpy as np
+
+    import oracle as O
+    from paper_1801_00338_gb300 import synth
+    g = synth.chung_lu_scaled(3000, 9000, 40_000, 2.1, 2.4, 5)
+    dU = np.bincount(g.u, minlength=g.nU).astype(np.float64)
+    dV = np.bincount(g.v, minlength=g.nV).astype(np.float64)
+    side = 1 if (dU * dU).sum() < (dV * dV).sum() else 0
+    n = g.nV if side else g.nU
+    val, cores, desc = bench.oracle_sample_all_cores(g, side, budget_s=30.0, cores=2)
+    assert cores == 2 and val > 0
+    P = O.Prepared(g.u, g.v, g.nU, g.nV, side)
+    _, paths = P.count(np.arange(n, dtype=np.uint32))
+    P.close()
+    assert f"{n} of {n} start vertices" in desc
+    assert f" {paths} 2-paths" in desc
