@@ -132,7 +132,7 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def AT_DEFAULT():
+def default_tuning():
     from paper_1801_00338_gb300 import autotune as AT
     return dict(AT.DEFAULT)
 
@@ -447,7 +447,7 @@ def run_own(args, rank, world, local_rank):
         "config": {"workload": WORKLOAD, "nU": nU, "nV": nV, "m": m, "W": W, "B": Bval, "start_side": "UV"[side],
                    "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (edge list 400 MB)",
                    "classes": ps["count"], "class_wedges": ps["work"],
-                   "tuning": dict(tuning or AT_DEFAULT(), **tune_info)},
+                   "tuning": dict(tuning or default_tuning(), **tune_info)},
         "e2e": {"value": whole_job_rate(world, W, e2e_ms), "unit": "wedges/s", "ms_per_step": e2e_ms,
                 "ms_per_step_min_max": [min(e2e_times), max(e2e_times)], "steps_timed": e2e_steps,
                 "h2d_bytes_per_step": 8 * m, "d2h_bytes_per_step": 8 * (nU + nV + m) + 16},

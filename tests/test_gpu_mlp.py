@@ -9,7 +9,6 @@ import math
 import numpy as np
 import pytest
 
-import oracle as O
 from oracle import mlp as M
 from paper_1801_00338_gb300 import synth
 
