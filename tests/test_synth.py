@@ -35,3 +35,14 @@ def test_uneven_batch_params():
     for nU, nV, m, gamma in ps:
         assert 1e3 * 0.99 <= m <= 1e6 * 1.01 and 1.9 <= gamma <= 3.0
         assert nU * nV >= 2 * m
+
+
+def test_batch_generation_does_not_depend_on_the_worker_count():
+    """The batched workload's graphs (and W) come out the same whether they are
+    drawn in one process or by a pool of spawned workers."""
+    from paper_1801_00338_gb300 import batch_eval
+    g1, W1 = batch_eval.generate(12, 5, 1e3, 2e4, workers=1)
+    g2, W2 = batch_eval.generate(12, 5, 1e3, 2e4, workers=2)
+    assert W1 == W2 and len(g1) == len(g2) == 12
+    for a, b in zip(g1, g2):
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and a[2:] == b[2:]
