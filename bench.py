@@ -202,7 +202,9 @@ def oracle_sample_all_cores(g, side: int, budget_s: float, cores: int = 0):
     import multiprocessing as mp
     import shutil
     import tempfile
-    cores = cores or (os.cpu_count() or 1)
+    # every process holds its own prepared copy of the graph (about 1.5 GB for
+    # 50M edges), so at most 32 of them
+    cores = cores or min(os.cpu_count() or 1, 32)
     n = g.nU if side == 0 else g.nV
     order = np.argsort(O_sample_keys(n)).astype(np.uint32)
     ctx = mp.get_context("spawn")
