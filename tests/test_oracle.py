@@ -95,6 +95,34 @@ def test_dense_random_graphs_vs_brute():
         assert (O.per_edge(u, v, nU, nV) == be).all()
 
 
+def test_per_edge_counts_as_a_matrix_product():
+    """With A the 0/1 matrix of U rows against V columns and C = A A^T (Lemma 1,
+    Eq. (2): C[v, w] = |Gamma_v ^ Gamma_w|), the definition of Section 2 gives
+    b_(v,x) = sum over w in Gamma_x, w != v, of (C[v, w] - 1), i.e. the entry
+    (v, x) of M A with M = C - 1 off the diagonal and 0 on it.  The oracle's
+    per-edge counts must equal it.  The product stays exact when M is split
+    into its low and high bytes, each multiplied by A in float32: every operand
+    is an integer below 256 (exact in bfloat16 too) and every partial sum of
+    one byte product stays below 2^24."""
+    for i in range(12):
+        nU, nV = 10 + 3 * i, 12 + 2 * i
+        m = (nU * nV) // (2 + i % 3)
+        u, v = synth.uniform_bipartite(nU, nV, m, 4000 + i)
+        A = np.zeros((nU, nV), np.int64)
+        A[u, v] = 1
+        C = A @ A.T
+        M = C - 1
+        np.fill_diagonal(M, 0)
+        M[C == 0] = 0  # pairs without a common neighbour meet no edge of the sum anyway
+        BE = M @ A
+        assert np.array_equal(BE[u, v].astype(np.uint64), O.per_edge(u, v, nU, nV))
+        lo = (M & 255).astype(np.float32)
+        hi = (M >> 8).astype(np.float32)
+        Af = A.astype(np.float32)
+        split = (hi @ Af).astype(np.int64) * 256 + (lo @ Af).astype(np.int64)
+        assert np.array_equal(split, BE)
+
+
 def test_printed_algorithm3_is_not_b_e():
     """Algorithm 3 as printed (sum of C(C[x], 2) over x in Gamma_v \\ {u}, C[x] counting
     2-paths from u) differs from the definition of b_e; the oracle follows the definition."""
