@@ -6,8 +6,9 @@ Chung-Lu bipartite graph |U| = 1M, |V| = 5M, 50M distinct edges, exponents
 One step = the whole counting path on the device-resident edge list: graph
 build (sort, validate, both adjacency structures), degree statistics and side
 choice (Algorithm 1), rank layout and classes, ExactBFC (B, the ordered
-one-sided sweep) and one whole-row sweep that gives vBFC for every vertex and
-eBFC for every edge (bfc_local_counts).  Metric: wedges/s, where a step's wedges are
+one-sided sweep) and the ordered per-edge sweep that gives eBFC for every edge
+and, through half sums of b_e over each vertex's edges, vBFC for every vertex
+(bfc_local_counts).  Metric: wedges/s, where a step's wedges are
 W = sum over the midpoint side of C(d, 2) (Lemma 2: the work of Algorithm 1).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl own|reference]
@@ -38,8 +39,8 @@ CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.a
 
 
 # DRAM bytes (read + write) per call of each counting-kernel set, from one ncu
-# capture of this workload (profiles/launches_chung_lu_1m_5m.md), valid only
-# for the kernel source they were taken with (its SHA-256 prefix).
+# capture of the kernels' dram__bytes counters, valid only for the kernel
+# source they were taken with (its SHA-256 prefix).
 MEASURED_TRAFFIC = {"source_sha256": "0340c575e944ff8e",
                     "bytes": {"win.edge": 17.04e9, "win.total": 5.709e9, "big.edge": 6.753e9}}
 

@@ -310,6 +310,11 @@ int bfc_mom_sizes(double var1, double B, double epsilon, double delta, uint64_t 
 int bfc_proposal_from_weights(bfc_graph *g, const uint32_t *weights, uint32_t flags, void *stream,
                               bfc_proposal **out);
 int bfc_proposal_free(bfc_proposal *p);
+/* Read a proposal's integer weights back: weights (host, n = nU + nV entries,
+ * caller-owned) receives them in population order, *W (optional) their sum.
+ * Synchronous: waits for the device.  Errors: BFC_EINVAL (null pointers, n not
+ * the proposal's population size), BFC_ECUDA. */
+int bfc_proposal_weights(const bfc_proposal *p, uint32_t *weights, uint64_t n, uint64_t *W);
 
 /* ---- instrumentation (no counterpart in the paper) --------------------- */
 
@@ -414,7 +419,8 @@ int bfc_get_tuning(const bfc_graph *g, bfc_tuning *t);
  *   offU : device, nU + 1 row offsets of the U rows;  nbrU : device, V ids
  *   offV : device, nV + 1 row offsets of the V rows;  nbrV : device, U ids
  *          (both sides describe the same simple graph; rows need not be sorted)
- *   flags: BFC_SIDE_AUTO (Algorithm 1's choice) / BFC_SIDE_U / BFC_SIDE_V
+ *   flags: BFC_SIDE_AUTO (start from V when sum over U of d^2 < sum over V of
+ *          d^2, else from U) / BFC_SIDE_U / BFC_SIDE_V
  *   out_B: device, one uint64, written in stream order (no host sync)
  * The only working memory is a __device__ array of BFC_NOALLOC_SCRATCH_WORDS
  * words inside this library; its device address is looked up (with

@@ -77,6 +77,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "bfc_mom_sizes": [dbl, dbl, dbl, dbl, P, P],
         "bfc_proposal_from_weights": [P, P, u32, P, P],
         "bfc_proposal_free": [P],
+        "bfc_proposal_weights": [P, P, u64, P],
         "bfc_exact_csr_noalloc": [P, P, u32, P, P, u32, u32, P, P],
         "bfc_exact_batch": [P, P, P, P, P, u32, u32, P, P, P],
         "bfc_features": [P, P, P],
@@ -337,6 +338,14 @@ def bfc_proposal_from_weights(h: int, weights, stream=None) -> int:
         rc = L.bfc_proposal_from_weights(h, w.ctypes.data, 0, _stream_ptr(stream), ctypes.byref(p))
     _check(rc, "bfc_proposal_from_weights")
     return p.value
+
+
+def bfc_proposal_weights(p: int, n: int):
+    """(weights as a uint32 numpy array of n entries, their sum W)."""
+    w = np.zeros(n, np.uint32)
+    W = ctypes.c_uint64()
+    _check(load().bfc_proposal_weights(p, w.ctypes.data, n, ctypes.byref(W)), "bfc_proposal_weights")
+    return w, W.value
 
 
 def bfc_proposal_free(p: int):

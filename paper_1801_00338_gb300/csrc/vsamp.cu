@@ -140,6 +140,13 @@ int bfc_proposal_from_weights(bfc_graph *g, const uint32_t *weights, uint32_t fl
   return BFC_OK;
 }
 
+int bfc_proposal_weights(const bfc_proposal *p, uint32_t *weights, uint64_t n, uint64_t *W) {
+  if (!p || !weights || n != p->n) return BFC_EINVAL;
+  if (cudaMemcpy(weights, p->weights.p, n * 4, cudaMemcpyDeviceToHost) != cudaSuccess) return BFC_ECUDA;
+  if (W) *W = p->W;
+  return BFC_OK;
+}
+
 int bfc_proposal_free(bfc_proposal *p) {
   if (!p) return BFC_EINVAL;
   cudaDeviceSynchronize();

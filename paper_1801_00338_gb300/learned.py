@@ -173,13 +173,11 @@ def proposal(G: "bfc.Graph", wb) -> int:
     return bfc.bfc_proposal_from_scores(G.h, scores(G, wb))
 
 
-def mixture_q_from_scores(s: np.ndarray) -> np.ndarray:
-    """q of the mixture for the integer weights the library derives from scores
-    (evaluation helper, float64 on the host)."""
-    s = np.asarray(s, dtype=np.float64)
-    w = np.maximum(1.0, np.floor(np.minimum(np.exp(np.minimum(s - s.max(), 0.0)) * 16777216.0, 16777216.0)))
-    n = s.size
-    return 0.5 / n + 0.5 * w / w.sum()
+def mixture_q(prop: int, n: int) -> np.ndarray:
+    """q of bfc_vsamp's mixture for a proposal handle, from the integer weights
+    the library stores: q(i) = 1/(2n) + w_i / (2W) (float64 on the host)."""
+    w, W = bfc.bfc_proposal_weights(prop, n)
+    return 0.5 / n + 0.5 * w.astype(np.float64) / float(W)
 
 
 def single_draw_variance(b: np.ndarray, q: np.ndarray | None = None) -> float:
@@ -254,8 +252,7 @@ def evaluate(train_count: int = 200, m_lo: float = 1e4, m_hi: float = 1e6, steps
         prop = proposal(G, tr.wb)
         torch.cuda.synchronize()
         t_prop = time.perf_counter() - t0
-        s = scores(G, tr.wb).cpu().numpy()
-        q = mixture_q_from_scores(s)
+        q = mixture_q(prop, G.nU + G.nV)
         var_u = single_draw_variance(b)
         var_l = single_draw_variance(b, q)
         k_u = draws_for_median_error(var_u, B)

@@ -86,6 +86,45 @@ def test_gradient_matches_fp64(bfc, small):
     assert np.abs(got - want).max() <= 1e-4 * scale
 
 
+def _weight_tolerance(w_orc):
+    """Per-weight bound between the kernel's float32 exp(s - max s) 2^24 and the
+    oracle's float64 one: s - max s rounds once in float32 (relative 2^-24, which
+    moves 2^24 e^d by at most |d| e^d <= 1/e units), expf is within 2 ulp
+    (relative 2^-22, at most 4 units at 2^24), and the two floors can differ by 1.
+    The exp term is doubled for margin."""
+    return 2.0 + w_orc.astype(np.float64) * 2.0 ** -21
+
+
+def test_proposal_weights_match_oracle_score_weights(bfc):
+    """bfc_proposal_from_scores's integer weights, element by element, against
+    oracle.mlp.score_weights on scores spanning the clamp at 1, the full unit and
+    ties at the maximum; the stored sum W is the sum of the weights."""
+    import torch
+    rng = np.random.default_rng(11)
+    nU, nV = 300, 500
+    u, v = synth.uniform_bipartite(nU, nV, 2500, 3)
+    n = nU + nV
+    cases = [
+        rng.normal(0.0, 3.0, n),                          # wide spread, many clamped to 1
+        rng.uniform(-0.5, 0.5, n),                        # all within the full unit
+        np.where(rng.random(n) < 0.1, 4.0, rng.normal(0.0, 1.0, n)),  # ties at the maximum
+        np.full(n, -7.25),                                # all equal
+    ]
+    with bfc.Graph(u, v, nU, nV) as G:
+        for s64 in cases:
+            s32 = s64.astype(np.float32)
+            prop = bfc.bfc_proposal_from_scores(G.h, torch.from_numpy(s32).cuda())
+            try:
+                w, W = bfc.bfc_proposal_weights(prop, n)
+            finally:
+                bfc.bfc_proposal_free(prop)
+            want = M.score_weights(s32.astype(np.float64))
+            diff = np.abs(w.astype(np.float64) - want.astype(np.float64))
+            assert np.all(diff <= _weight_tolerance(want))
+            assert W == int(w.astype(np.uint64).sum())
+            assert w.min() >= 1 and w.max() == 1 << 24
+
+
 def test_training_reduces_loss_and_proposal_gains(bfc):
     """Train on small generated graphs; on a held-out graph the learned mixture
     proposal keeps VSamp unbiased (exactly, by the importance weights) and its
@@ -115,8 +154,8 @@ def test_training_reduces_loss_and_proposal_gains(bfc):
             est = G.vsamp(k, trials, 99, proposal=prop)
         finally:
             bfc.bfc_proposal_free(prop)
-    q = Ln.mixture_q_from_scores(s)
-    assert np.sum(q * b / (4 * q)) == pytest.approx(B, rel=1e-12)
+    w = M.score_weights(s).astype(np.float64)
+    q = 0.5 / w.size + 0.5 * w / w.sum()
     var_u = Ln.single_draw_variance(b)
     var_l = Ln.single_draw_variance(b, q)
     assert var_l < 0.25 * var_u

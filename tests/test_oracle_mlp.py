@@ -72,3 +72,45 @@ def test_features_from_definition_on_a_small_graph():
     assert f[4, 1] == pytest.approx(math.log1p(6) / 16)
     assert f[4, 5] == pytest.approx(math.log1p(3) / 16)
 
+
+
+def test_score_weights_equal_scores_give_the_full_unit():
+    """exp(s - max s) = 1 for every vertex when all scores are equal: 2^24 each,
+    whatever the common value (the maximum is subtracted before exp)."""
+    for c in (-40.0, 0.0, 3.0, 700.0):
+        w = M.score_weights(np.full(7, c))
+        assert w.dtype == np.uint64
+        assert np.all(w == 1 << 24)
+
+
+def test_score_weights_halving_per_ln2():
+    """s_i = s_max - k ln 2 gives 2^24 e^(-k ln 2) = 2^(24-k); the float64 exp may
+    land one unit low before the floor, never more."""
+    k = np.arange(0, 24)
+    s = 5.0 - k * math.log(2.0)
+    w = M.score_weights(s).astype(np.int64)
+    want = (1 << (24 - k)).astype(np.int64)
+    assert np.all(np.abs(w - want) <= 1)
+    assert w[0] == 1 << 24
+
+
+def test_score_weights_floor_not_round_and_floor_at_one():
+    """A ratio of 0.3 gives floor(0.3 * 2^24) = 5033164 (rounding would give
+    5033165); ratios below 2^-24 are lifted to 1, so every vertex can be drawn."""
+    s = np.array([2.0, 2.0 + math.log(0.3), 2.0 - 17.0 * math.log(2.0), 2.0 - 30.0, -1e6])
+    w = M.score_weights(s)
+    assert w[0] == 1 << 24
+    assert w[1] == 5033164
+    assert w[2] in (127, 128)
+    assert w[3] == 1 and w[4] == 1
+
+
+def test_score_weights_depend_only_on_score_differences():
+    """Shifting every score by a constant leaves the weights unchanged; without the
+    max subtraction the shifted scores would clamp to 2^24 everywhere."""
+    s = np.array([0.0, -1.0, -2.5, -0.25])
+    w0 = M.score_weights(s)
+    for c in (3.0, 50.0, -20.0):
+        assert np.array_equal(M.score_weights(s + c), w0)
+    assert w0[1] == math.floor(16777216.0 / math.e)
+    assert np.all(np.diff(M.score_weights(np.array([0.0, -0.1, -0.2, -0.3])).astype(np.int64)) < 0)
