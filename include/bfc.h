@@ -385,6 +385,15 @@ int bfc_profile_read(const char *tag, uint64_t *launches, double *total_ms);
  *                     wedge lists 32 targets at a time when they hold at most
  *                     this many targets per start-row entry on average;
  *                     default 64, BFC_TUNE_NO_FLAT never.
+ *   hl_max_light    : a window-class start vertex of the ordered sweeps
+ *                     (bfc_exact, and the per-edge and per-vertex counts
+ *                     without BFC_WHOLE_ROWS) whose wedge lists other than its
+ *                     longest hold at most this many wedges is counted without
+ *                     windows: those lists in a shared-memory hash table, the
+ *                     longest one streamed once against it.  Default 0: as
+ *                     many as the table holds at half load (2,048 in the
+ *                     512-thread CTAs, 4,096 in the 1,024-thread ones);
+ *                     BFC_TUNE_NO_HL never.
  * A changed class limit redoes the cached classification of the start
  * vertices on the next counting call (the rank layout is kept).
  * Errors: BFC_EINVAL (null handle, a value out of range). */
@@ -395,9 +404,11 @@ typedef struct bfc_tuning {
   uint32_t tau;
   uint32_t local_sweep;
   uint32_t flat_max_avg;
+  uint32_t hl_max_light;
 } bfc_tuning;
 #define BFC_TUNE_NO_HUBS 0xFFFFFFFFu
 #define BFC_TUNE_NO_FLAT 0xFFFFFFFFu
+#define BFC_TUNE_NO_HL   0xFFFFFFFFu
 /* t == NULL restores every default. */
 int bfc_set_tuning(bfc_graph *g, const bfc_tuning *t);
 /* The settings in effect, with the class-limit defaults filled in. */

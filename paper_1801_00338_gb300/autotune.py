@@ -32,7 +32,8 @@ from . import bfc
 
 NO_HUBS = bfc.BFC_TUNE_NO_HUBS
 NO_FLAT = bfc.BFC_TUNE_NO_FLAT
-DEFAULT = {"warp_max_wedges": 512, "small_max_segs": 512, "hubs": 0, "tau": 0, "local_sweep": 0, "flat_max_avg": 64}
+DEFAULT = {"warp_max_wedges": 512, "small_max_segs": 512, "hubs": 0, "tau": 0, "local_sweep": 0, "flat_max_avg": 64,
+           "hl_max_light": 0}
 # log-space distance under which another graph's cached choice is a starting point
 NEAR = 0.25
 
@@ -90,6 +91,8 @@ def candidates(knob: str, base: dict, info: dict) -> list[int]:
         return [0, 1]
     if knob == "flat_max_avg":
         return [64, NO_FLAT, 16, 32, 128, 256]
+    if knob == "hl_max_light":
+        return [0, bfc.BFC_TUNE_NO_HL, 1024, 2048]
     raise ValueError(knob)
 
 
@@ -98,7 +101,7 @@ def knobs_for(ops) -> list[str]:
     ks = []
     if "exact" in ops:
         ks += ["hubs", "tau"]
-    ks += ["small_max_segs", "warp_max_wedges", "flat_max_avg"]
+    ks += ["hl_max_light", "small_max_segs", "warp_max_wedges", "flat_max_avg"]
     if "local" in ops:
         ks += ["local_sweep"]
     return ks

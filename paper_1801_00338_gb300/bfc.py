@@ -32,7 +32,8 @@ BFC_HUB_MMA = 0x200
 BFC_HUB_MAX = 16384
 BFC_TUNE_NO_HUBS = 0xFFFFFFFF
 BFC_TUNE_NO_FLAT = 0xFFFFFFFF
-TUNING_FIELDS = ("warp_max_wedges", "small_max_segs", "hubs", "tau", "local_sweep", "flat_max_avg")
+BFC_TUNE_NO_HL = 0xFFFFFFFF
+TUNING_FIELDS = ("warp_max_wedges", "small_max_segs", "hubs", "tau", "local_sweep", "flat_max_avg", "hl_max_light")
 
 
 class bfc_tuning(ctypes.Structure):
@@ -185,6 +186,9 @@ def bfc_profile_read(tag: str) -> tuple[int, float]:
 
 PROFILE_TAGS = [f"{c}.{m}" for c in ("warp", "win", "big") for m in ("total", "edge", "single", "local")]
 PROFILE_TAGS += ["hub.total", "hub.degree", "hub.light", "esamp.exact", "esamp.fast", "wsamp"]
+# the window kernels also per class: "win.edge.s8" (8-bit counters, 512-thread CTAs)
+WIN_CLASS_TAGS = [f"win.{m}.{c}" for m in ("total", "edge", "single", "local")
+                  for c in ("s2", "s4", "s8", "s16", "s32", "l2", "l4", "l8", "l16", "l32")]
 # kernel tag -> the classes it runs
 TAG_CLASSES = {"warp": ("warp",), "win": ("s2", "s4", "s8", "s16", "s32", "l2", "l4", "l8", "l16", "l32"),
                "big": ("big",)}

@@ -44,6 +44,7 @@
 // {v, w} x {x, y} is seen from the wedge v - x - w once for each of its two
 // midpoints.
 #include <algorithm>
+#include <string>
 #include <vector>
 
 #include "bfc_internal.cuh"
@@ -110,6 +111,7 @@ struct WArgs {
   const uint32_t *vert_of;
   const uint64_t *work;  // wedges walked from each start rank (the ordered suffixes)
   uint32_t flat_max;     // flat expansion limit (targets per start-row entry), BFC_TUNE_NO_FLAT: never
+  uint32_t hl_max;       // heavy-light split limit (light wedges per start vertex), 0: never
   const uint32_t *list;
   uint32_t list_n;
   unsigned int *queue;
@@ -494,6 +496,210 @@ __device__ __forceinline__ void count_flat(const WArgs &a, uint32_t r, uint64_t 
   __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// heavy-light split of one start vertex (ordered TOTAL and EDGE modes)
+// ---------------------------------------------------------------------------
+// On power-law midpoint sides most of a low-degree start vertex's wedges come
+// from one wedge list: its heaviest midpoint row.  A target w with c(v, w) >= 2
+// lies in at least one of the other ("light") lists, so with c_L(w) the count
+// over the light lists and h(w) = [w in the heavy list],
+//   sum_w C(c, 2) = sum_w C(c_L, 2) + sum_{w in heavy} c_L(w)      (Eq. (3))
+// The light lists are counted in a shared-memory hash table (keys w + 1, so
+// an all-zero table is empty); the heavy list is streamed once against it
+// with read-only lookups: a miss (c_L = 0) adds nothing to any output.  EDGE:
+// a heavy hit flags its slot (h = 1), then the light lists read back
+// c = c_L + h; a heavy wedge v - x - w adds c - 1 = c_L to both its edges.
+// The table holds at most half as many keys as slots, so every probe
+// sequence ends at an empty slot or the key.
+constexpr uint32_t HL_FLAG = 0x80000000u;
+#ifndef HL_U
+#define HL_U 4
+#endif
+#ifndef HL_UL
+#define HL_UL 4
+#endif
+__device__ __forceinline__ uint32_t hl_slot(uint32_t key, int shift) { return (key * 0x9E3779B1u) >> shift; }
+__device__ __forceinline__ int hl_insert(uint32_t *keys, uint32_t mask, int shift, uint32_t key) {
+  uint32_t s = hl_slot(key, shift);
+  for (uint32_t p = 0; p <= mask; p++) {
+    uint32_t k = reinterpret_cast<volatile uint32_t *>(keys)[s];
+    if (k == key) return (int)s;
+    if (k == 0u) {
+      k = atomicCAS(&keys[s], 0u, key);
+      if (k == 0u || k == key) return (int)s;
+    }
+    s = (s + 1) & mask;
+  }
+  return -1;
+}
+__device__ __forceinline__ int hl_find(const uint32_t *keys, uint32_t mask, int shift, uint32_t key) {
+  uint32_t s = hl_slot(key, shift);
+  for (uint32_t p = 0; p <= mask; p++) {
+    const uint32_t k = keys[s];
+    if (k == key) return (int)s;
+    if (k == 0u) return -1;
+    s = (s + 1) & mask;
+  }
+  return -1;
+}
+// row of light element t: the last row l with pre[l] <= t (pre[d] = total)
+__device__ __forceinline__ uint32_t hl_row(const uint32_t *pre, uint32_t d, uint32_t t) {
+  uint32_t lo = 0, hi = d;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (pre[mid] <= t) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Count start vertex r (rows [rb, re), 1 <= re - rb <= THREADS) by the split
+// above if its light lists hold at most tmax / 2 wedges; returns false (after
+// a barrier, nothing written) otherwise.  ctr: the WORDS zeroed counter words (left
+// zeroed); area: 4 THREADS + 4 free words (8-byte aligned); sh_hmax: a shared
+// word the caller zeroed before the vertex.  All threads call it together.
+template <int MODE, int THREADS, uint32_t WORDS>
+__device__ __forceinline__ bool count_hl(const WArgs &a, uint64_t rb, uint64_t re, uint64_t work, uint32_t *ctr,
+                                         uint32_t tmax, uint32_t *area, unsigned long long *sh_hmax,
+                                         uint32_t *sh_wt, uint64_t &acc) {
+  constexpr int NW = THREADS / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t d = (uint32_t)(re - rb), j = threadIdx.x;
+  uint32_t b = 0, len = 0;
+  if (j < d) {
+    const uint32_t x = a.sX[rb + j];
+    b = a.sB[rb + j];
+    len = (uint32_t)a.offM[x + 1] - b;
+  }
+  // the heaviest row, the lowest index among equals
+  unsigned long long key = (j < d) ? (((unsigned long long)len << 16) | (0xFFFFu - j)) : 0ull;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, key, o);
+    key = y > key ? y : key;
+  }
+  if (lane == 0) atomicMax(sh_hmax, key);
+  __syncthreads();
+  const unsigned long long hk = *sh_hmax;
+  const uint32_t hlen = (uint32_t)(hk >> 16), hj = 0xFFFFu - (uint32_t)(hk & 0xFFFFu);
+  const uint64_t wl = work - hlen;
+  if (2 * wl > tmax) return false;
+  uint32_t T = 64;
+  while (T < 2 * wl) T <<= 1;
+  int logT = 6;
+  while ((1u << logT) < T) logT++;
+  const uint32_t mask = T - 1;
+  const int shift = 32 - logT;
+  uint32_t *keys = ctr, *cnt = ctr + T;
+  // a bitmap of the light keys after the table (the largest power of two of
+  // words that fits, at most 8,192): most heavy targets are not light, and one
+  // bit test turns them away without walking a probe sequence
+  uint32_t nbw = 4;
+  while (nbw * 2 <= (uint32_t)(WORDS - 2 * T) && nbw < 8192) nbw <<= 1;
+  uint32_t *bits = ctr + 2 * T;
+  int logB = 7;
+  while ((1u << logB) < nbw * 32) logB++;
+  const int bshift = 32 - logB;
+  uint32_t *pre = area, *beg = area + THREADS + 2;
+  unsigned long long *rs = reinterpret_cast<unsigned long long *>(area + 2 * THREADS + 4);
+  // prefix sums of the light rows' lengths
+  const uint32_t ll = (j < d && j != hj) ? len : 0u;
+  const uint32_t inc = warp_incl_scan_u32(ll);
+  if (lane == 31) sh_wt[warp] = inc;
+  if (j < d) {
+    beg[j] = b;
+    if (MODE == MODE_EDGE) rs[j] = 0;
+  }
+  __syncthreads();
+  uint32_t base = 0, total = 0;
+#pragma unroll 4
+  for (int w = 0; w < NW; w++) {
+    const uint32_t t = sh_wt[w];
+    base += (w < warp) ? t : 0u;
+    total += t;
+  }
+  if (j < d) pre[j] = base + inc - ll;
+  if (j == 0) pre[d] = total;
+  __syncthreads();
+  // count sweep over the light lists, HL_UL elements in flight per thread
+  for (uint32_t t0 = j; t0 < total; t0 += HL_UL * THREADS) {
+    uint32_t w[HL_UL];
+#pragma unroll
+    for (int k = 0; k < HL_UL; k++) {
+      const uint32_t t = t0 + k * THREADS;
+      w[k] = 0xFFFFFFFFu;
+      if (t < total) {
+        const uint32_t l = hl_row(pre, d, t);
+        w[k] = __ldg(&a.mR[beg[l] + (t - pre[l])]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < HL_UL; k++) {
+      if (w[k] == 0xFFFFFFFFu) continue;
+      const int sl = hl_insert(keys, mask, shift, w[k] + 1u);
+      if (sl >= 0) acc += atomicAdd(&cnt[sl], 1u);
+      else atomicOr(a.err, DERR_CAPACITY);
+      const uint32_t bi = ((w[k] + 1u) * 0x85EBCA6Bu) >> bshift;
+      atomicOr(&bits[bi >> 5], 1u << (bi & 31));
+    }
+  }
+  __syncthreads();
+  // the heavy list, HL_U loads in flight per thread
+  const uint32_t hb = beg[hj];
+  uint64_t rsh = 0;
+  for (uint32_t t0 = j; t0 < hlen; t0 += HL_U * THREADS) {
+    uint32_t w[HL_U];
+#pragma unroll
+    for (int k = 0; k < HL_U; k++) {
+      const uint32_t t = t0 + k * THREADS;
+      w[k] = (t < hlen) ? __ldg(&a.mR[hb + t]) : 0xFFFFFFFFu;
+    }
+#pragma unroll
+    for (int k = 0; k < HL_U; k++) {
+      if (w[k] == 0xFFFFFFFFu) continue;
+      const uint32_t bi = ((w[k] + 1u) * 0x85EBCA6Bu) >> bshift;
+      if (!((bits[bi >> 5] >> (bi & 31)) & 1u)) continue;
+      const int sl = hl_find(keys, mask, shift, w[k] + 1u);
+      if (sl >= 0) {
+        const uint32_t c = cnt[sl];
+        acc += c;
+        if (MODE == MODE_EDGE) {
+          cnt[sl] = c | HL_FLAG;
+          rsh += c;
+          atomicAdd(&a.beM[hb + t0 + k * THREADS], (unsigned long long)c);
+        }
+      }
+    }
+  }
+  if (MODE == MODE_EDGE) {
+    rsh = warp_sum_u64(rsh);
+    if (lane == 0 && rsh) atomicAdd(&rs[hj], (unsigned long long)rsh);
+    // the read sweep adds c - 1 > 0 only where some c reached 2
+    if (__syncthreads_or(acc != 0)) {
+      for (uint32_t t = j; t < total; t += THREADS) {
+        const uint32_t l = hl_row(pre, d, t);
+        const uint32_t i = beg[l] + (t - pre[l]);
+        const int sl = hl_find(keys, mask, shift, __ldg(&a.mR[i]) + 1u);
+        if (sl < 0) { atomicOr(a.err, DERR_CAPACITY); continue; }
+        const uint32_t v = cnt[sl];
+        const uint32_t c = (v & ~HL_FLAG) + (v >> 31);
+        if (c > 1) {
+          atomicAdd(&rs[l], (unsigned long long)(c - 1));
+          atomicAdd(&a.beM[i], (unsigned long long)(c - 1));
+        }
+      }
+      __syncthreads();
+      if (j < d && rs[j]) atomicAdd(&a.be[a.sEid[rb + j]], rs[j]);
+    }
+  } else {
+    __syncthreads();
+  }
+  // back to an all-zero table
+  uint4 *c4 = reinterpret_cast<uint4 *>(ctr);
+  for (uint32_t i = j; i < (2 * T + nbw) / 4; i += THREADS) c4[i] = make_uint4(0, 0, 0, 0);
+  __syncthreads();
+  return true;
+}
+
 template <int MODE, int CW, int P>
 __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win(WArgs a) {
   constexpr int WIN_THREADS = WinCfg<P>::THREADS;
@@ -510,9 +716,14 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win
   __shared__ uint32_t sh_min[2];
   __shared__ unsigned long long sh_win[2];
   __shared__ uint32_t sh_idx, sh_carry;
-  __shared__ unsigned long long sh_acc;
+  __shared__ unsigned long long sh_acc, sh_hmax;
   __shared__ uint32_t wtot[32];
   constexpr int NW = WIN_THREADS / 32;
+  // heavy-light table slots: the largest power of two <= a quarter of the
+  // counter words (keys and counts take half, the bitmap at least a quarter)
+  constexpr uint32_t HL_TMAX = (WIN_WORDS / 4 >= 8192) ? 8192u : 4096u;
+  static_assert(2 * HL_TMAX + 4 <= WIN_WORDS, "table and bitmap fit the counter words");
+  static_assert(5 * WIN_SMAX >= 4 * WIN_THREADS + 4, "heavy-light scratch fits the segment tables");
   constexpr uint32_t Z = C::Z;
   // B accumulates at increment time (the sum of old values is C(c, 2))
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -524,6 +735,7 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win
       sh_idx = atomicAdd(a.queue, 1u);
       sh_carry = 0;
       sh_acc = 0;
+      sh_hmax = 0;
       sh_min[0] = INF_RANK; sh_win[0] = 0;
       sh_min[1] = INF_RANK; sh_win[1] = 0;
     }
@@ -535,7 +747,14 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win
     const uint64_t rb = a.offR[r], re = (r < a.rank_end) ? a.offR[r + 1] : rb;  // ranks >= rank_end: done elsewhere
     const uint32_t lo0 = Full<MODE>::value ? 0u : r + 1;
     uint64_t acc = 0;  // per thread, over the whole vertex
-    if ((uint64_t)a.nS <= (uint64_t)lo0 + Z && a.flat_max != BFC_TUNE_NO_FLAT &&
+    bool done = false;
+    if ((MODE == MODE_TOTAL || MODE == MODE_EDGE) && a.hl_max && re > rb && re - rb <= (uint64_t)WIN_THREADS)
+      done = count_hl<MODE, WIN_THREADS, WIN_WORDS>(a, rb, re, a.work[r], ctr,
+                                         (uint32_t)umin64(HL_TMAX, 2ull * a.hl_max), sm + WIN_WORDS, &sh_hmax,
+                                         wtot, acc);
+    if (done) {
+      // counted by the heavy-light split
+    } else if ((uint64_t)a.nS <= (uint64_t)lo0 + Z && a.flat_max != BFC_TUNE_NO_FLAT &&
         a.work[r] <= (uint64_t)a.flat_max * (re - rb)) {
       // ---- every later rank fits in one window and the lists are short:
       // no segments, no window walk
@@ -1058,8 +1277,13 @@ static int launch_lists(bfc_graph *g, WArgs a, const uint32_t *const *lists, con
     const int threads = small ? WinCfg<P_SMALL>::THREADS : WinCfg<P_LARGE>::THREADS;
     const size_t smem = small ? WinCfg<P_SMALL>::SMEM : WinCfg<P_LARGE>::SMEM;
     BFC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // per-class timing as well ("win.edge.s8": the 8-bit small-window class)
+    static const char *cls_names[10] = {"s2", "s4", "s8", "s16", "s32", "l2", "l4", "l8", "l16", "l32"};
+    const std::string ctag = std::string(tag_of(1, MODE)) + "." + cls_names[c - CLS_S0];
+    profile_begin(ctag.c_str(), s);
     kern<<<cap((unsigned)(sms * per_sm), c), threads, smem, s>>>(w);
     BFC_LAUNCHED();
+    profile_end(ctag.c_str(), s);
   }
   if (any_win) profile_end(tag_of(1, MODE), s);
   if (have(CLS_BIG) && big_cap > 0) {
@@ -1103,6 +1327,7 @@ static WArgs args_of(bfc_graph *g, Plan &p) {
   a.vert_of = ptr<uint32_t>(p.vert_of);
   a.work = ptr<uint64_t>(p.work);
   a.flat_max = g->tune.flat_max_avg ? g->tune.flat_max_avg : FLAT_MAX_AVG;
+  a.hl_max = g->tune.hl_max_light == BFC_TUNE_NO_HL ? 0u : g->tune.hl_max_light ? g->tune.hl_max_light : 0xFFFFFFFFu;
   a.err = ptr<uint32_t>(g->err);
   return a;
 }

@@ -22,11 +22,11 @@ def fake_measure(best: dict, counts=(7, 7, 28), log=None):
 
 def test_descent_finds_the_separable_minimum():
     target = {"warp_max_wedges": 128, "small_max_segs": 256, "hubs": 2048, "tau": 20, "local_sweep": 1,
-              "flat_max_avg": 32}
+              "flat_max_avg": 32, "hl_max_light": 1024}
     best, ms, tried, counts = A.coordinate_descent(fake_measure(target), A.knobs_for(("exact", "local")),
                                                    dict(A.DEFAULT), INFO)
     assert best == target and ms == 1.0
-    assert tried[0] == (A.DEFAULT, 7.0)
+    assert tried[0] == (A.DEFAULT, 8.0)
     assert counts == (7, 7, 28)
 
 
@@ -58,7 +58,8 @@ def test_hub_candidates_are_whole_tiles_within_bounds():
 
 def test_cache_round_trip_and_reuse(tmp_path):
     path = str(tmp_path / "t.json")
-    target = {"warp_max_wedges": 256, "small_max_segs": 128, "hubs": 0, "tau": 0, "local_sweep": 1, "flat_max_avg": 64}
+    target = {"warp_max_wedges": 256, "small_max_segs": 128, "hubs": 0, "tau": 0, "local_sweep": 1, "flat_max_avg": 64,
+              "hl_max_light": 0}
     log = []
     r1 = A.tune(fake_measure(target, log=log), "GB300", SIG, INFO, ("exact", "local"), path)
     assert r1.source == "search" and r1.tuning == target and r1.default_ms == 4.0
@@ -79,7 +80,7 @@ def test_cache_round_trip_and_reuse(tmp_path):
 def test_near_graph_starts_from_the_cached_choice(tmp_path):
     path = str(tmp_path / "t.json")
     target = {"warp_max_wedges": 256, "small_max_segs": 128, "hubs": 2048, "tau": 0, "local_sweep": 0,
-              "flat_max_avg": 64}
+              "flat_max_avg": 64, "hl_max_light": 0}
     A.tune(fake_measure(target), "GB300", SIG, INFO, ("exact", "local"), path)
     near = dict(SIG, m=int(SIG["m"] * 1.1))
     log = []

@@ -11,11 +11,13 @@ pytestmark = pytest.mark.gpu
 
 NO_HUBS = 0xFFFFFFFF
 NO_FLAT = 0xFFFFFFFF
+NO_HL = 0xFFFFFFFF
 # extreme and typical settings: every vertex past the warp class in the large
 # windows or the big class (small_max_segs = 1), almost no warp class
 # (warp_max_wedges = 1), hub blocks of one tile and of none, the densest
 # column threshold, whole-row local counts, and the flat expansion of
-# single-window vertices never or always taken
+# single-window vertices never or always taken, and the heavy-light split
+# never, for almost no vertex, or up to a middle limit
 TUNINGS = [
     {},
     {"small_max_segs": 1},
@@ -28,6 +30,10 @@ TUNINGS = [
     {"flat_max_avg": NO_FLAT},
     {"flat_max_avg": 0xFFFFFFFE},
     {"flat_max_avg": 0xFFFFFFFE, "local_sweep": 1},
+    {"hl_max_light": NO_HL},
+    {"hl_max_light": 1},
+    {"hl_max_light": 300, "small_max_segs": 1},
+    {"hl_max_light": NO_HL, "flat_max_avg": NO_FLAT},
 ]
 
 
