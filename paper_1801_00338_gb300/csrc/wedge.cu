@@ -11,14 +11,15 @@
 // vBFC costs O(|Gamma^2_v|)) and by their degree (which bounds every c(v, w)):
 //   skip   degree < 2 or nothing after it: every c <= 1, contributes 0
 //   warp   <= 512 wedges: one warp per vertex, open addressing in shared memory
-//   small windows (<= 512 wedge-list segments of 256 targets): a 512-thread
-//          CTA (three per SM) with 16,384 counter words in shared memory
-//   large windows (<= 1,536 segments): a 1,024-thread CTA with 49,152 words
+//   small windows (<= 256 wedge-list segments of 512 targets): a 256-thread
+//          CTA (six per SM) with 8,192 counter words in shared memory
+//   large windows (<= 1,280 segments): a 512-thread CTA (three per SM) with
+//          12,288 words
 //   big    more segments: the large CTA with its segment cursors in global
 //          memory and a 32-bit window
 // The window classes pack their counters by degree: 2 bits for degree <= 3,
-// 4 for <= 15, 8 for <= 255, 16 for <= 65,535, else 32, so a 16,384-word
-// window spans 262,144 ranks at 2 bits and 16,384 at 32.  Ranks ascend with
+// 4 for <= 15, 8 for <= 255, 16 for <= 65,535, else 32, so an 8,192-word
+// window spans 131,072 ranks at 2 bits and 8,192 at 32.  Ranks ascend with
 // degree, so the low-rank vertices, which walk the most of the rank space,
 // are exactly the ones with the narrowest counters and the widest windows.
 // The thresholds are scheduling settings (bfc_tuning); the counts do not
@@ -31,7 +32,11 @@
 // EDGE and LOCAL modes a read sweep of the same pieces against the final
 // counts, and a clear of the counter words.  A vertex whose later ranks all
 // fit in one window and whose lists are short skips the walk and expands its
-// lists 32 targets at a time (count_flat).
+// lists 32 targets at a time (count_flat).  In the ordered TOTAL and EDGE
+// modes a vertex first tries the heavy-light split (count_hl): its lists other
+// than the longest in a small hash table, the longest streamed once against
+// it; in EDGE mode a vertex whose other lists are too long for the table walks
+// the windows with the longest list as their heavy list (heavy_piece).
 //
 // Modes: TOTAL (B only), EDGE (b_e; the vertex counts follow from b_e),
 // SINGLE (Algorithm 2 on a batch of vertices: every w != v, whole midpoint
@@ -63,33 +68,38 @@ constexpr int CW_OF[5] = {2, 4, 8, 16, 32};
 constexpr int WH_WARPS = 8;
 constexpr int WH_SLOTS = 1024;                    // per warp
 constexpr uint64_t WH_MAX_WORK = WH_SLOTS / 2;    // load factor <= 1/2
-// window kernels come in two sizes (tag P_SMALL / P_LARGE).  Small: three
-// 512-thread CTAs per SM (48 warps: the dependent row loads every window
-// starts with need many warps in flight), each with 16,384 counter words and
-// room for 512 wedge-list segments; measured faster than four 256-thread CTAs
-// with 12,288 words, four 384-thread ones, or two 512-thread ones with twice
-// the window.  Large: one 1,024-thread CTA per SM with 49,152 words and 1,536
-// segments, for the vertices whose wedge lists need more segments.
+// window kernels come in two sizes (tag P_SMALL / P_LARGE).  A CTA runs one
+// start vertex at a time through a chain of dependent phases (row loads,
+// segment table, each window's count, read and clear, each closed by a CTA
+// barrier), so many small CTAs per SM hide that chain better than a few large
+// ones.  Small: six 256-thread CTAs per SM, each with 8,192 counter words and
+// room for 256 wedge-list segments (of 512 targets); measured faster than
+// three 512-thread CTAs with 16,384 words, four 384-thread ones, five
+// 256-thread ones with 512 segments, or eight 192-thread ones.  Large: three
+// 512-thread CTAs per SM with 12,288 words and 1,280 segments, for the
+// vertices whose wedge lists need more segments (one 1,024-thread CTA per SM
+// measured twice as slow).
 template <int P>
 struct WinCfg;
 template <>
-struct WinCfg<4> {  // small: 3 CTAs of 16 warps per SM, 64 KB windows
-  static constexpr int THREADS = 512;
-  static constexpr int MINB = 3;
-  static constexpr uint32_t WORDS = 16 * 1024;
-  static constexpr uint32_t SMAX = 512;
+struct WinCfg<4> {  // small: 6 CTAs of 8 warps per SM, 32 KB windows
+  static constexpr int THREADS = 256;
+  static constexpr int MINB = 6;
+  static constexpr uint32_t WORDS = 8 * 1024;
+  static constexpr uint32_t SMAX = 256;
   static constexpr size_t SMEM = (size_t)WORDS * 4 + (size_t)SMAX * 5 * 4;
 };
 template <>
-struct WinCfg<1> {  // large: one CTA of 32 warps per SM, 192 KB windows
-  static constexpr int THREADS = 1024;
-  static constexpr int MINB = 1;
-  static constexpr uint32_t WORDS = 48 * 1024;
-  static constexpr uint32_t SMAX = 1536;
+struct WinCfg<1> {  // large: 3 CTAs of 16 warps per SM, 48 KB windows
+  static constexpr int THREADS = 512;
+  static constexpr int MINB = 3;
+  static constexpr uint32_t WORDS = 12 * 1024;
+  static constexpr uint32_t SMAX = 1280;
   static constexpr size_t SMEM = (size_t)WORDS * 4 + (size_t)SMAX * 5 * 4;
 };
 constexpr int P_SMALL = 4, P_LARGE = 1;
-constexpr uint32_t SEG = 256;                     // wedge-list segment (elements)
+constexpr uint32_t SEG = 512;                     // wedge-list segment (elements)
+constexpr uint32_t HEAVY_SEG = 0x80000000u;       // segment-row flag: a segment of the heavy list
 // big class (segment cursors in global memory)
 constexpr int CT_THREADS = 1024;
 constexpr uint32_t CT_WORDS = 48 * 1024;          // 192 KB of counter words
@@ -152,6 +162,7 @@ __device__ __forceinline__ void resolve_list(WArgs &a) {
 }
 
 __device__ __forceinline__ uint64_t umin64(uint64_t x, uint64_t y) { return x < y ? x : y; }
+__device__ __forceinline__ uint32_t umax32(uint32_t x, uint32_t y) { return x > y ? x : y; }
 // modes that walk whole midpoint rows (every w != v) rather than the part after v
 template <int MODE>
 struct Full { static constexpr bool value = (MODE == MODE_SINGLE || MODE == MODE_LOCAL); };
@@ -362,6 +373,57 @@ __device__ __forceinline__ void count_segment(const uint32_t *__restrict__ mR, u
         const uint32_t first_out = __shfl_sync(0xffffffffu, w[k], n & 31);
         nx = (cur < end) ? first_out : INF_RANK;
         return;
+      }
+    }
+  }
+}
+
+// The heavy list in a window (the split of count_hl with windows): the
+// vertex's longest wedge list is not counted; after the window's light counts
+// are final, the warp walks one of its segments from cur.  Targets below lo
+// lie where no light list has a target (c_L = 0) and are passed over; a
+// target w in [lo, hi) adds c_L(w) = peek(w - lo) to acc, and in EDGE mode
+// raises its counter by one (so the read sweep sees c = c_L + 1) and adds c_L
+// to the far edge (staged at beM[i]) and to the returned near-edge sum (valid
+// in lane 0).  On return cur is the first target >= hi (or end), nx its rank
+// (INF_RANK at the end), hit whether some c_L was > 0.
+template <int MODE, int CW, uint32_t WIN_WORDS>
+__device__ __forceinline__ uint64_t heavy_piece(const uint32_t *__restrict__ mR, unsigned long long *beM,
+                                                uint32_t &cur, uint32_t end, uint32_t lo, uint32_t hi, uint32_t *ctr,
+                                                uint32_t &nx, uint64_t &acc, bool &hit) {
+  using C = Ctr<CW, WIN_WORDS>;
+  const int lane = threadIdx.x & 31;
+  uint64_t rs = 0;
+  while (true) {
+    const uint32_t base = cur;
+    uint32_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const uint32_t i = base + k * 32 + lane;
+      w[k] = (i < end) ? __ldg(&mR[i]) : INF_RANK;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const bool in = w[k] < hi;
+      const uint32_t bal = __ballot_sync(0xffffffffu, in);
+      if (in && w[k] >= lo) {
+        const uint32_t c = C::peek(ctr, w[k] - lo);
+        if (c) {
+          acc += c;
+          hit = true;
+          if (MODE == MODE_EDGE) {
+            C::inc_get(ctr, w[k] - lo);
+            rs += c;
+            atomicAdd(&beM[base + k * 32 + lane], (unsigned long long)c);
+          }
+        }
+      }
+      const uint32_t n = __popc(bal);
+      cur += n;
+      if (n < 32) {
+        const uint32_t first_out = __shfl_sync(0xffffffffu, w[k], n & 31);
+        nx = (cur < end) ? first_out : INF_RANK;
+        return warp_sum_u64(rs);
       }
     }
   }
@@ -583,22 +645,20 @@ __device__ __forceinline__ bool count_hl(const WArgs &a, uint64_t rb, uint64_t r
   const uint32_t hlen = (uint32_t)(hk >> 16), hj = 0xFFFFu - (uint32_t)(hk & 0xFFFFu);
   const uint64_t wl = work - hlen;
   if (2 * wl > tmax) return false;
-  uint32_t T = 64;
-  while (T < 2 * wl) T <<= 1;
-  int logT = 6;
-  while ((1u << logT) < T) logT++;
+  // T: the smallest power of two >= max(2 wl, 64)
+  const uint32_t need = umax32(2u * (uint32_t)wl, 64u);
+  const int logT = 32 - __clz(need - 1u);
+  const uint32_t T = 1u << logT;
   const uint32_t mask = T - 1;
   const int shift = 32 - logT;
   uint32_t *keys = ctr, *cnt = ctr + T;
   // a bitmap of the light keys after the table (the largest power of two of
   // words that fits, at most 8,192): most heavy targets are not light, and one
   // bit test turns them away without walking a probe sequence
-  uint32_t nbw = 4;
-  while (nbw * 2 <= (uint32_t)(WORDS - 2 * T) && nbw < 8192) nbw <<= 1;
+  const int lognbw = min(31 - __clz(WORDS - 2 * T), 13);
+  const uint32_t nbw = 1u << lognbw;
   uint32_t *bits = ctr + 2 * T;
-  int logB = 7;
-  while ((1u << logB) < nbw * 32) logB++;
-  const int bshift = 32 - logB;
+  const int bshift = 32 - (lognbw + 5);
   uint32_t *pre = area, *beg = area + THREADS + 2;
   unsigned long long *rs = reinterpret_cast<unsigned long long *>(area + 2 * THREADS + 4);
   // prefix sums of the light rows' lengths
@@ -610,13 +670,11 @@ __device__ __forceinline__ bool count_hl(const WArgs &a, uint64_t rb, uint64_t r
     if (MODE == MODE_EDGE) rs[j] = 0;
   }
   __syncthreads();
-  uint32_t base = 0, total = 0;
-#pragma unroll 4
-  for (int w = 0; w < NW; w++) {
-    const uint32_t t = sh_wt[w];
-    base += (w < warp) ? t : 0u;
-    total += t;
-  }
+  // warp totals -> this warp's base and the grand total, by one warp scan
+  const uint32_t wt = (lane < NW) ? sh_wt[lane] : 0u;
+  const uint32_t wincl = warp_incl_scan_u32(wt);
+  const uint32_t base = __shfl_sync(0xffffffffu, wincl - wt, warp);
+  const uint32_t total = __shfl_sync(0xffffffffu, wincl, 31);
   if (j < d) pre[j] = base + inc - ll;
   if (j == 0) pre[d] = total;
   __syncthreads();
@@ -717,11 +775,12 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win
   __shared__ unsigned long long sh_win[2];
   __shared__ uint32_t sh_idx, sh_carry;
   __shared__ unsigned long long sh_acc, sh_hmax;
+  __shared__ uint32_t sh_hj;  // the vertex's heavy list (row index), INF_RANK: none
   __shared__ uint32_t wtot[32];
   constexpr int NW = WIN_THREADS / 32;
   // heavy-light table slots: the largest power of two <= a quarter of the
   // counter words (keys and counts take half, the bitmap at least a quarter)
-  constexpr uint32_t HL_TMAX = (WIN_WORDS / 4 >= 8192) ? 8192u : 4096u;
+  constexpr uint32_t HL_TMAX = (WIN_WORDS / 4 >= 4096) ? 4096u : (WIN_WORDS / 4 >= 2048) ? 2048u : 1024u;
   static_assert(2 * HL_TMAX + 4 <= WIN_WORDS, "table and bitmap fit the counter words");
   static_assert(5 * WIN_SMAX >= 4 * WIN_THREADS + 4, "heavy-light scratch fits the segment tables");
   constexpr uint32_t Z = C::Z;
@@ -736,6 +795,7 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win
       sh_carry = 0;
       sh_acc = 0;
       sh_hmax = 0;
+      sh_hj = INF_RANK;
       sh_min[0] = INF_RANK; sh_win[0] = 0;
       sh_min[1] = INF_RANK; sh_win[1] = 0;
     }
@@ -748,10 +808,16 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win
     const uint32_t lo0 = Full<MODE>::value ? 0u : r + 1;
     uint64_t acc = 0;  // per thread, over the whole vertex
     bool done = false;
-    if ((MODE == MODE_TOTAL || MODE == MODE_EDGE) && a.hl_max && re > rb && re - rb <= (uint64_t)WIN_THREADS)
+    if ((MODE == MODE_TOTAL || MODE == MODE_EDGE) && a.hl_max && re > rb && re - rb <= (uint64_t)WIN_THREADS) {
       done = count_hl<MODE, WIN_THREADS, WIN_WORDS>(a, rb, re, a.work[r], ctr,
                                          (uint32_t)umin64(HL_TMAX, 2ull * a.hl_max), sm + WIN_WORDS, &sh_hmax,
                                          wtot, acc);
+      // otherwise, in EDGE mode, the longest list is walked as the heavy list of
+      // the windows (it spares the read sweep of that list; in TOTAL mode the
+      // extra barrier per window measured slower)
+      if (MODE == MODE_EDGE && !done && re - rb > 1 && threadIdx.x == 0)
+        sh_hj = 0xFFFFu - (uint32_t)(sh_hmax & 0xFFFFu);
+    }
     if (done) {
       // counted by the heavy-light split
     } else if ((uint64_t)a.nS <= (uint64_t)lo0 + Z && a.flat_max != BFC_TUNE_NO_FLAT &&
@@ -793,7 +859,7 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win
         s_end[s] = min(e, sb + SEG);
         s_ps[s] = sb;
         s_nx[s] = 0;  // unknown: load it
-        s_row[s] = (uint32_t)(j - rb);
+        s_row[s] = (uint32_t)(j - rb) | ((uint32_t)(j - rb) == sh_hj ? HEAVY_SEG : 0u);
       }
       __syncthreads();
     }
@@ -811,7 +877,7 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win
         bool act = false;
         if (sl < nseg) {
           const uint32_t c0 = s_cur[sl];
-          my_nx = (c0 < s_end[sl]) ? s_nx[sl] : INF_RANK;
+          my_nx = (c0 < s_end[sl] && !(s_row[sl] & HEAVY_SEG)) ? s_nx[sl] : INF_RANK;
           act = my_nx < hi;  // 0: next target not loaded yet
           s_ps[sl] = c0;     // nothing of it counted in this window yet
         }
@@ -848,13 +914,37 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win
         sh_win[par ^ 1] = 0;
       }
       const uint32_t nm = sh_min[par];
+      // ---- the heavy list against the window's final light counts
+      if (sh_hj != INF_RANK) {
+        bool hit = false;
+        for (uint32_t s0 = warp; s0 < nseg; s0 += NW * 32) {
+          const uint32_t sl = s0 + (uint32_t)lane * NW;
+          const bool act = sl < nseg && (s_row[sl] & HEAVY_SEG) && s_cur[sl] < s_end[sl] && s_nx[sl] < hi;
+          uint32_t bal = __ballot_sync(0xffffffffu, act);
+          while (bal) {
+            const int l = __ffs(bal) - 1;
+            bal &= bal - 1;
+            const uint32_t sg = s0 + (uint32_t)l * NW;
+            uint32_t cur = s_cur[sg], nx = INF_RANK;
+            const uint64_t rs = heavy_piece<MODE, CW, WIN_WORDS>(a.mR, a.beM, cur, s_end[sg], lo, hi, ctr, nx, acc,
+                                                                 hit);
+            if (lane == 0) {
+              s_cur[sg] = cur;
+              s_nx[sg] = nx;
+              if (MODE == MODE_EDGE && rs) atomicAdd(&a.be[a.sEid[rb + sh_hj]], (unsigned long long)rs);
+            }
+          }
+        }
+        if (MODE == MODE_EDGE && __any_sync(0xffffffffu, hit) && lane == 0) atomicAdd(&sh_win[par], 1ull);
+        __syncthreads();
+      }
       // ---- EDGE / LOCAL: every wedge of the window reads its final count
       if (MODE == MODE_EDGE || MODE == MODE_LOCAL) {
         if (sh_win[par]) {
           // the same ownership: each warp reads back the pieces it counted
           for (uint32_t s0 = warp; s0 < nseg; s0 += NW * 32) {
             const uint32_t sl = s0 + (uint32_t)lane * NW;
-            const bool act = sl < nseg && s_ps[sl] < s_cur[sl];
+            const bool act = sl < nseg && s_ps[sl] < s_cur[sl] && !(s_row[sl] & HEAVY_SEG);
             uint32_t bal = __ballot_sync(0xffffffffu, act);
             while (bal) {
               const int l = __ffs(bal) - 1;
@@ -862,7 +952,8 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win
               const uint32_t sg = s0 + (uint32_t)l * NW;
               const uint64_t rowsum = read_piece<MODE>(a.mR, a.beM, s_ps[sg], s_cur[sg], lo,
                                                         [&](uint32_t idx) { return C::peek(ctr, idx); });
-              if (lane == 0 && rowsum) atomicAdd(&a.be[a.sEid[rb + s_row[sg]]], (unsigned long long)rowsum);
+              if (lane == 0 && rowsum)
+                atomicAdd(&a.be[a.sEid[rb + (s_row[sg] & ~HEAVY_SEG)]], (unsigned long long)rowsum);
             }
           }
           __syncthreads();

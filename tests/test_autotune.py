@@ -21,7 +21,7 @@ def fake_measure(best: dict, counts=(7, 7, 28), log=None):
 
 
 def test_descent_finds_the_separable_minimum():
-    target = {"warp_max_wedges": 128, "small_max_segs": 256, "hubs": 2048, "tau": 20, "local_sweep": 1,
+    target = {"warp_max_wedges": 128, "small_max_segs": 128, "hubs": 2048, "tau": 20, "local_sweep": 1,
               "flat_max_avg": 32, "hl_max_light": 1024}
     best, ms, tried, counts = A.coordinate_descent(fake_measure(target), A.knobs_for(("exact", "local")),
                                                    dict(A.DEFAULT), INFO)
