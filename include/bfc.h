@@ -366,11 +366,13 @@ int bfc_profile_read(const char *tag, uint64_t *launches, double *total_ms);
  *                     shared-memory hash table; 1..512, default 512 (the
  *                     table's capacity at load factor 1/2).
  *   small_max_segs  : the others whose wedge lists hold at most this many
- *                     segments of 512 wedges (plus one per row) run in the
- *                     256-thread window CTAs (six per SM, 32 KB counter
- *                     windows); above it, up to 1,280 segments, in the
- *                     512-thread CTAs (three per SM, 48 KB windows), and
- *                     beyond that in the big-class kernel; 1..256, default 256.
+ *                     segments of 512 wedges (plus one per row), or who have
+ *                     at most half this many rows (their segments are then
+ *                     lengthened), run in the 128-thread window CTAs (twelve
+ *                     per SM, 16 KB counter windows); the rest, up to 1,280
+ *                     segments or 640 rows, in the 512-thread CTAs (three per
+ *                     SM, 48 KB windows), and beyond that in the big-class
+ *                     kernel; 1..128, default 128.
  *   hubs            : hub count of bfc_exact with BFC_HUB_MMA: 0 the automatic
  *                     choice (bfc_exact_hub with hubs = 0), BFC_TUNE_NO_HUBS
  *                     none (the walk counts every pair), else a multiple of
@@ -391,7 +393,8 @@ int bfc_profile_read(const char *tag, uint64_t *launches, double *total_ms);
  *                     longest hold at most this many wedges is counted without
  *                     windows: those lists in a shared-memory hash table, the
  *                     longest one streamed once against it.  Default 0: as
- *                     many as the table holds at half load (1,024);
+ *                     many as the table holds at half load (512 in the 128-thread CTAs,
+ *                     1,024 in the 512-thread ones);
  *                     BFC_TUNE_NO_HL never.
  * A changed class limit redoes the cached classification of the start
  * vertices on the next counting call (the rank layout is kept).

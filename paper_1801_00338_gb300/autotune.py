@@ -32,7 +32,7 @@ from . import bfc
 
 NO_HUBS = bfc.BFC_TUNE_NO_HUBS
 NO_FLAT = bfc.BFC_TUNE_NO_FLAT
-DEFAULT = {"warp_max_wedges": 512, "small_max_segs": 256, "hubs": 0, "tau": 0, "local_sweep": 0, "flat_max_avg": 64,
+DEFAULT = {"warp_max_wedges": 512, "small_max_segs": 128, "hubs": 0, "tau": 0, "local_sweep": 0, "flat_max_avg": 64,
            "hl_max_light": 0}
 # log-space distance under which another graph's cached choice is a starting point
 NEAR = 0.25
@@ -84,7 +84,7 @@ def candidates(knob: str, base: dict, info: dict) -> list[int]:
         vals = [0] + [v for v in (t // 2, 2 * t) if v >= 2]
         return sorted(set(vals), key=vals.index)
     if knob == "small_max_segs":
-        return [256, 192, 128, 64, 32]
+        return [128, 96, 64, 32]
     if knob == "warp_max_wedges":
         return [512, 256, 128]
     if knob == "local_sweep":

@@ -131,7 +131,7 @@ struct Plan {
   uint32_t big_seg_cap = 0;           // segment capacity of the big class
   // class limits the classification was made with (bfc_tuning's
   // warp_max_wedges and small_max_segs; wedge.cu caps them)
-  uint32_t warp_max = 512, small_max = 256;
+  uint32_t warp_max = 512, small_max = 128;
   uint64_t total_work = 0;     // sum of work = W of the midpoint side
   uint32_t max_deg_S = 0;
 };

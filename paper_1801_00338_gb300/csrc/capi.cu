@@ -227,7 +227,7 @@ int bfc_set_tuning(bfc_graph *g, const bfc_tuning *t) {
     g->tune = bfc_tuning{};
     return BFC_OK;
   }
-  if (t->warp_max_wedges > 512 || t->small_max_segs > 256 || t->tau == 1 || t->local_sweep > 1) return BFC_EINVAL;
+  if (t->warp_max_wedges > 512 || t->small_max_segs > 128 || t->tau == 1 || t->local_sweep > 1) return BFC_EINVAL;
   if (t->hubs != 0 && t->hubs != BFC_TUNE_NO_HUBS && (t->hubs % 128 || t->hubs > BFC_HUB_MAX)) return BFC_EINVAL;
   g->tune = *t;
   return BFC_OK;
@@ -237,7 +237,7 @@ int bfc_get_tuning(const bfc_graph *g, bfc_tuning *t) {
   if (!g || !t) return BFC_EINVAL;
   *t = g->tune;
   if (!t->warp_max_wedges) t->warp_max_wedges = 512;
-  if (!t->small_max_segs) t->small_max_segs = 256;
+  if (!t->small_max_segs) t->small_max_segs = 128;
   if (!t->flat_max_avg) t->flat_max_avg = 64;
   return BFC_OK;
 }

@@ -423,7 +423,7 @@ int plan_classify(bfc_graph *g, Plan &p, cudaStream_t s);  // wedge.cu
 // class limits of the graph's tuning (0 = the default)
 static void tuned_limits(const bfc_graph *g, uint32_t *warp_max, uint32_t *small_max) {
   *warp_max = g->tune.warp_max_wedges ? g->tune.warp_max_wedges : 512u;
-  *small_max = g->tune.small_max_segs ? g->tune.small_max_segs : 256u;
+  *small_max = g->tune.small_max_segs ? g->tune.small_max_segs : 128u;
 }
 
 int plan_build(bfc_graph *g, int side, cudaStream_t s) {

@@ -11,15 +11,16 @@
 // vBFC costs O(|Gamma^2_v|)) and by their degree (which bounds every c(v, w)):
 //   skip   degree < 2 or nothing after it: every c <= 1, contributes 0
 //   warp   <= 512 wedges: one warp per vertex, open addressing in shared memory
-//   small windows (<= 256 wedge-list segments of 512 targets): a 256-thread
-//          CTA (six per SM) with 8,192 counter words in shared memory
-//   large windows (<= 1,280 segments): a 512-thread CTA (three per SM) with
-//          12,288 words
-//   big    more segments: the large CTA with its segment cursors in global
-//          memory and a 32-bit window
+//   small windows (<= 128 wedge-list segments of 512 targets, or at most 64
+//          rows with longer segments): a 128-thread CTA (twelve per SM) with
+//          4,096 counter words in shared memory
+//   large windows (<= 1,280 segments, or at most 640 rows): a 512-thread CTA
+//          (three per SM) with 12,288 words
+//   big    more: the large CTA with its segment cursors in global memory and a
+//          32-bit window
 // The window classes pack their counters by degree: 2 bits for degree <= 3,
-// 4 for <= 15, 8 for <= 255, 16 for <= 65,535, else 32, so an 8,192-word
-// window spans 131,072 ranks at 2 bits and 8,192 at 32.  Ranks ascend with
+// 4 for <= 15, 8 for <= 255, 16 for <= 65,535, else 32, so a 4,096-word
+// window spans 65,536 ranks at 2 bits and 4,096 at 32.  Ranks ascend with
 // degree, so the low-rank vertices, which walk the most of the rank space,
 // are exactly the ones with the narrowest counters and the widest windows.
 // The thresholds are scheduling settings (bfc_tuning); the counts do not
@@ -72,21 +73,23 @@ constexpr uint64_t WH_MAX_WORK = WH_SLOTS / 2;    // load factor <= 1/2
 // start vertex at a time through a chain of dependent phases (row loads,
 // segment table, each window's count, read and clear, each closed by a CTA
 // barrier), so many small CTAs per SM hide that chain better than a few large
-// ones.  Small: six 256-thread CTAs per SM, each with 8,192 counter words and
-// room for 256 wedge-list segments (of 512 targets); measured faster than
-// three 512-thread CTAs with 16,384 words, four 384-thread ones, five
-// 256-thread ones with 512 segments, or eight 192-thread ones.  Large: three
+// ones.  Small: twelve 128-thread CTAs per SM, each with 4,096 counter words
+// and room for 128 wedge-list segments; measured faster than six 256-thread
+// CTAs with 8,192 words, three 512-thread ones with 16,384 words, four
+// 384-thread ones or eight 192-thread ones.  A vertex of at most half as many
+// rows as segments fits any window class whatever its wedge count: its
+// segments are lengthened (seg_len_for).  Large: three
 // 512-thread CTAs per SM with 12,288 words and 1,280 segments, for the
 // vertices whose wedge lists need more segments (one 1,024-thread CTA per SM
 // measured twice as slow).
 template <int P>
 struct WinCfg;
 template <>
-struct WinCfg<4> {  // small: 6 CTAs of 8 warps per SM, 32 KB windows
-  static constexpr int THREADS = 256;
-  static constexpr int MINB = 6;
-  static constexpr uint32_t WORDS = 8 * 1024;
-  static constexpr uint32_t SMAX = 256;
+struct WinCfg<4> {  // small: 12 CTAs of 4 warps per SM, 16 KB windows
+  static constexpr int THREADS = 128;
+  static constexpr int MINB = 12;
+  static constexpr uint32_t WORDS = 4 * 1024;
+  static constexpr uint32_t SMAX = 128;
   static constexpr size_t SMEM = (size_t)WORDS * 4 + (size_t)SMAX * 5 * 4;
 };
 template <>
@@ -99,7 +102,15 @@ struct WinCfg<1> {  // large: 3 CTAs of 16 warps per SM, 48 KB windows
 };
 constexpr int P_SMALL = 4, P_LARGE = 1;
 constexpr uint32_t SEG = 512;                     // wedge-list segment (elements)
-constexpr uint32_t HEAVY_SEG = 0x80000000u;       // segment-row flag: a segment of the heavy list
+// Segment length of an ordered-sweep start vertex with d rows and w wedges in
+// a window class of smax segments: SEG, or longer so that the segments fit
+// (sum_rows ceil(len / L) <= d + w / L <= smax for L >= w / (smax - d)).
+__host__ __device__ __forceinline__ uint32_t seg_len_for(uint64_t w, uint64_t d, uint32_t smax) {
+  if (d >= smax) return SEG;
+  const uint64_t need = (w + (smax - d) - 1) / (smax - d);
+  return need <= SEG ? SEG : (uint32_t)(need < 0x40000000ull ? need : 0x40000000ull);
+}
+
 // big class (segment cursors in global memory)
 constexpr int CT_THREADS = 1024;
 constexpr uint32_t CT_WORDS = 48 * 1024;          // 192 KB of counter words
@@ -181,6 +192,12 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
   return x;  // valid in lane 0
+}
+// The same sum, by one 32-bit warp reduction when every lane's value is below
+// 2^27 (the per-piece sums nearly always are); valid in lane 0.
+__device__ __forceinline__ uint64_t warp_sum_u64_small(uint64_t x) {
+  if (__all_sync(0xffffffffu, x < (1ull << 27))) return __reduce_add_sync(0xffffffffu, (uint32_t)x);
+  return warp_sum_u64(x);
 }
 
 // ---------------------------------------------------------------------------
@@ -423,7 +440,7 @@ __device__ __forceinline__ uint64_t heavy_piece(const uint32_t *__restrict__ mR,
       if (n < 32) {
         const uint32_t first_out = __shfl_sync(0xffffffffu, w[k], n & 31);
         nx = (cur < end) ? first_out : INF_RANK;
-        return warp_sum_u64(rs);
+        return warp_sum_u64_small(rs);
       }
     }
   }
@@ -459,7 +476,7 @@ __device__ __forceinline__ uint64_t read_piece(const uint32_t *__restrict__ mR, 
       }
     }
   }
-  return warp_sum_u64(rowsum);
+  return warp_sum_u64_small(rowsum);
 }
 
 // Expand the wedge lists of start-row entries [cb, ce) (at most 32, one per
@@ -768,7 +785,7 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win
   extern __shared__ uint32_t sm[];
   uint32_t *ctr = sm;
   uint32_t *s_cur = sm + WIN_WORDS, *s_end = s_cur + WIN_SMAX, *s_ps = s_end + WIN_SMAX, *s_nx = s_ps + WIN_SMAX;
-  uint32_t *s_row = s_nx + WIN_SMAX;
+  uint32_t *s_row = s_nx + WIN_SMAX;  // canonical id of the segment's start-row edge
   // window state, double buffered by window parity so that a window needs
   // two barriers: one after counting, one after clearing
   __shared__ uint32_t sh_min[2];
@@ -776,6 +793,8 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win
   __shared__ uint32_t sh_idx, sh_carry;
   __shared__ unsigned long long sh_acc, sh_hmax;
   __shared__ uint32_t sh_hj;  // the vertex's heavy list (row index), INF_RANK: none
+  __shared__ uint32_t sh_heid;  // its start-row edge id (the segments' s_row), INF_RANK: none
+  __shared__ uint32_t sh_seglen;  // segment length of the vertex (ordered modes)
   __shared__ uint32_t wtot[32];
   constexpr int NW = WIN_THREADS / 32;
   // heavy-light table slots: the largest power of two <= a quarter of the
@@ -796,6 +815,7 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win
       sh_acc = 0;
       sh_hmax = 0;
       sh_hj = INF_RANK;
+      sh_heid = INF_RANK;
       sh_min[0] = INF_RANK; sh_win[0] = 0;
       sh_min[1] = INF_RANK; sh_win[1] = 0;
     }
@@ -808,6 +828,7 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win
     const uint32_t lo0 = Full<MODE>::value ? 0u : r + 1;
     uint64_t acc = 0;  // per thread, over the whole vertex
     bool done = false;
+    if (!Full<MODE>::value && threadIdx.x == 0) sh_seglen = seg_len_for(a.work[r], re - rb, WIN_SMAX);
     if ((MODE == MODE_TOTAL || MODE == MODE_EDGE) && a.hl_max && re > rb && re - rb <= (uint64_t)WIN_THREADS) {
       done = count_hl<MODE, WIN_THREADS, WIN_WORDS>(a, rb, re, a.work[r], ctr,
                                          (uint32_t)umin64(HL_TMAX, 2ull * a.hl_max), sm + WIN_WORDS, &sh_hmax,
@@ -817,6 +838,8 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win
       // extra barrier per window measured slower)
       if (MODE == MODE_EDGE && !done && re - rb > 1 && threadIdx.x == 0)
         sh_hj = 0xFFFFu - (uint32_t)(sh_hmax & 0xFFFFu);
+    } else if (!Full<MODE>::value) {
+      __syncthreads();  // sh_seglen (count_hl's first barrier publishes it otherwise)
     }
     if (done) {
       // counted by the heavy-light split
@@ -832,14 +855,17 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win
       for (uint32_t i = threadIdx.x; i < (used + 3) / 4; i += WIN_THREADS) c4[i] = make_uint4(0, 0, 0, 0);
     } else {
     // ---- segments of the vertex's wedge lists
+    const uint32_t seglen = Full<MODE>::value ? SEG : sh_seglen;
     for (uint64_t base = rb; base < re; base += WIN_THREADS) {
       const uint64_t j = base + threadIdx.x;
-      uint32_t b = 0, e = 0, ns = 0;
+      uint32_t b = 0, e = 0, ns = 0, eid = 0;
       if (j < re) {
         const uint32_t x = a.sX[j];
         b = Full<MODE>::value ? (uint32_t)a.offM[x] : a.sB[j];
         e = (uint32_t)a.offM[x + 1];
-        ns = (e - b + SEG - 1) / SEG;
+        ns = (e - b + seglen - 1) / seglen;
+        eid = a.sEid[j];
+        if ((uint32_t)(j - rb) == sh_hj) sh_heid = eid;
       }
       const uint32_t incl = warp_incl_scan_u32(ns);
       if (lane == 31) wtot[warp] = incl;
@@ -854,12 +880,12 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win
       for (uint32_t k = 0; k < ns; k++) {
         const uint32_t s = first + k;
         if (s >= WIN_SMAX) { atomicOr(a.err, DERR_CAPACITY); break; }
-        const uint32_t sb = b + k * SEG;
+        const uint32_t sb = b + k * seglen;
         s_cur[s] = sb;
-        s_end[s] = min(e, sb + SEG);
+        s_end[s] = min(e, sb + seglen);
         s_ps[s] = sb;
         s_nx[s] = 0;  // unknown: load it
-        s_row[s] = (uint32_t)(j - rb) | ((uint32_t)(j - rb) == sh_hj ? HEAVY_SEG : 0u);
+        s_row[s] = eid;
       }
       __syncthreads();
     }
@@ -877,7 +903,7 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win
         bool act = false;
         if (sl < nseg) {
           const uint32_t c0 = s_cur[sl];
-          my_nx = (c0 < s_end[sl] && !(s_row[sl] & HEAVY_SEG)) ? s_nx[sl] : INF_RANK;
+          my_nx = (c0 < s_end[sl] && s_row[sl] != sh_heid) ? s_nx[sl] : INF_RANK;
           act = my_nx < hi;  // 0: next target not loaded yet
           s_ps[sl] = c0;     // nothing of it counted in this window yet
         }
@@ -919,7 +945,7 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win
         bool hit = false;
         for (uint32_t s0 = warp; s0 < nseg; s0 += NW * 32) {
           const uint32_t sl = s0 + (uint32_t)lane * NW;
-          const bool act = sl < nseg && (s_row[sl] & HEAVY_SEG) && s_cur[sl] < s_end[sl] && s_nx[sl] < hi;
+          const bool act = sl < nseg && s_row[sl] == sh_heid && s_cur[sl] < s_end[sl] && s_nx[sl] < hi;
           uint32_t bal = __ballot_sync(0xffffffffu, act);
           while (bal) {
             const int l = __ffs(bal) - 1;
@@ -931,7 +957,7 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win
             if (lane == 0) {
               s_cur[sg] = cur;
               s_nx[sg] = nx;
-              if (MODE == MODE_EDGE && rs) atomicAdd(&a.be[a.sEid[rb + sh_hj]], (unsigned long long)rs);
+              if (MODE == MODE_EDGE && rs) atomicAdd(&a.be[sh_heid], (unsigned long long)rs);
             }
           }
         }
@@ -944,7 +970,7 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win
           // the same ownership: each warp reads back the pieces it counted
           for (uint32_t s0 = warp; s0 < nseg; s0 += NW * 32) {
             const uint32_t sl = s0 + (uint32_t)lane * NW;
-            const bool act = sl < nseg && s_ps[sl] < s_cur[sl] && !(s_row[sl] & HEAVY_SEG);
+            const bool act = sl < nseg && s_ps[sl] < s_cur[sl] && s_row[sl] != sh_heid;
             uint32_t bal = __ballot_sync(0xffffffffu, act);
             while (bal) {
               const int l = __ffs(bal) - 1;
@@ -953,7 +979,7 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win
               const uint64_t rowsum = read_piece<MODE>(a.mR, a.beM, s_ps[sg], s_cur[sg], lo,
                                                         [&](uint32_t idx) { return C::peek(ctr, idx); });
               if (lane == 0 && rowsum)
-                atomicAdd(&a.be[a.sEid[rb + (s_row[sg] & ~HEAVY_SEG)]], (unsigned long long)rowsum);
+                atomicAdd(&a.be[s_row[sg]], (unsigned long long)rowsum);
             }
           }
           __syncthreads();
@@ -1148,19 +1174,23 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_big(WArgs a) {
 // segments the small windows.  Both are capped by the tables' capacities.
 struct ClsLimits {
   uint32_t warp_max, small_max;
+  // ordered plans: a window class also takes any vertex of at most half its
+  // segment capacity in rows, with segments lengthened to fit (seg_len_for)
+  bool adaptive;
 };
-static ClsLimits limits_of(const Plan &p) {
+static ClsLimits limits_of(const Plan &p, bool adaptive = true) {
   return ClsLimits{std::min<uint32_t>(p.warp_max, (uint32_t)WH_MAX_WORK),
-                   std::min<uint32_t>(std::max<uint32_t>(p.small_max, 1u), WinCfg<P_SMALL>::SMAX)};
+                   std::min<uint32_t>(std::max<uint32_t>(p.small_max, 1u), WinCfg<P_SMALL>::SMAX), adaptive};
 }
 
 __device__ __forceinline__ uint32_t class_of(uint64_t d, uint64_t w, ClsLimits lim) {
   if (d < 2 || w == 0) return CLS_SKIP;
   if (w <= lim.warp_max) return CLS_WARP;
   const uint64_t segs = d + w / SEG + 1;
+  constexpr uint32_t LMAX = WinCfg<P_LARGE>::SMAX;
   uint32_t base;
-  if (segs <= lim.small_max) base = CLS_S0;
-  else if (segs <= WinCfg<P_LARGE>::SMAX) base = CLS_L0;
+  if (segs <= lim.small_max || (lim.adaptive && 2 * d <= lim.small_max)) base = CLS_S0;
+  else if (segs <= LMAX || (lim.adaptive && 2 * d <= LMAX)) base = CLS_L0;
   else return CLS_BIG;
   // counter width: every c(v, w) <= degree of v
   if (d <= 3) return base + 0;
@@ -1482,7 +1512,7 @@ static int full_rows_batch(bfc_graph *g, Plan &p, int mode, const uint32_t *item
   unsigned int *cursor = counts + 32;                                                 // [32, 48)
   unsigned long long *maxseg = reinterpret_cast<unsigned long long *>(counts + 48);
   k_item_classify<<<grid_for((uint64_t)n_items * 32, 256), 256, 0, s>>>(item_rank, n_items, ptr<uint64_t>(p.offR),
-                                                                        ptr<uint32_t>(p.sX), p.offM, limits_of(p),
+                                                                        ptr<uint32_t>(p.sX), p.offM, limits_of(p, false),
                                                                         ptr<uint32_t>(cls_of), counts, maxseg, out);
   count_launch();
   unsigned int hc[16];

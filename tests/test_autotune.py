@@ -21,7 +21,7 @@ def fake_measure(best: dict, counts=(7, 7, 28), log=None):
 
 
 def test_descent_finds_the_separable_minimum():
-    target = {"warp_max_wedges": 128, "small_max_segs": 128, "hubs": 2048, "tau": 20, "local_sweep": 1,
+    target = {"warp_max_wedges": 128, "small_max_segs": 64, "hubs": 2048, "tau": 20, "local_sweep": 1,
               "flat_max_avg": 32, "hl_max_light": 1024}
     best, ms, tried, counts = A.coordinate_descent(fake_measure(target), A.knobs_for(("exact", "local")),
                                                    dict(A.DEFAULT), INFO)
@@ -39,7 +39,7 @@ def test_descent_only_touches_the_workloads_settings():
 
 def test_a_setting_that_changes_a_count_is_rejected():
     def measure(t):
-        return 1.0, (5,) if t["small_max_segs"] != 128 else (6,)
+        return 1.0, (5,) if t["small_max_segs"] != 64 else (6,)
     with pytest.raises(RuntimeError, match="counts differ"):
         A.coordinate_descent(measure, ["small_max_segs"], dict(A.DEFAULT), INFO)
 
@@ -58,7 +58,7 @@ def test_hub_candidates_are_whole_tiles_within_bounds():
 
 def test_cache_round_trip_and_reuse(tmp_path):
     path = str(tmp_path / "t.json")
-    target = {"warp_max_wedges": 256, "small_max_segs": 128, "hubs": 0, "tau": 0, "local_sweep": 1, "flat_max_avg": 64,
+    target = {"warp_max_wedges": 256, "small_max_segs": 64, "hubs": 0, "tau": 0, "local_sweep": 1, "flat_max_avg": 64,
               "hl_max_light": 0}
     log = []
     r1 = A.tune(fake_measure(target, log=log), "GB300", SIG, INFO, ("exact", "local"), path)
@@ -79,7 +79,7 @@ def test_cache_round_trip_and_reuse(tmp_path):
 
 def test_near_graph_starts_from_the_cached_choice(tmp_path):
     path = str(tmp_path / "t.json")
-    target = {"warp_max_wedges": 256, "small_max_segs": 128, "hubs": 2048, "tau": 0, "local_sweep": 0,
+    target = {"warp_max_wedges": 256, "small_max_segs": 64, "hubs": 2048, "tau": 0, "local_sweep": 0,
               "flat_max_avg": 64, "hl_max_light": 0}
     A.tune(fake_measure(target), "GB300", SIG, INFO, ("exact", "local"), path)
     near = dict(SIG, m=int(SIG["m"] * 1.1))

@@ -26,7 +26,7 @@ TUNINGS = [
     {"hubs": 128, "tau": 2},
     {"hubs": 1024},
     {"hubs": NO_HUBS},
-    {"local_sweep": 1, "small_max_segs": 200},
+    {"local_sweep": 1, "small_max_segs": 100},
     {"flat_max_avg": NO_FLAT},
     {"flat_max_avg": 0xFFFFFFFE},
     {"flat_max_avg": 0xFFFFFFFE, "local_sweep": 1},
