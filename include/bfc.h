@@ -342,6 +342,15 @@ int bfc_trim_memory(void);
  * expected to leave its handles usable after such a failure. */
 int bfc_fail_alloc_after(int64_t n);
 
+/* Wait limit for tests of the timeout path: the device-side waits of the
+ * tensor-core hub kernel (bfc_exact_hub, bfc_exact with BFC_HUB_MMA) give up
+ * after ns nanoseconds of GPU global time instead of the built-in one second
+ * (ns = 0 restores it).  A kernel that gives up stops issuing work, waits for
+ * the copies and tensor-core operations it already issued, releases its
+ * tensor memory and exits, and its call returns BFC_ETIMEOUT; the handle
+ * stays usable.  Process-wide; applies to launches made after the call. */
+int bfc_set_wait_limit(uint64_t ns);
+
 /* Device timing of the library's counting kernels: when enabled, every
  * wedge-kernel launch is bracketed by CUDA events on the launch stream.
  * bfc_profile_read synchronises on the recorded events and returns, for the

@@ -99,6 +99,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         f.restype = i32
     L.bfc_fail_alloc_after.argtypes = [ctypes.c_int64]
     L.bfc_fail_alloc_after.restype = i32
+    L.bfc_set_wait_limit.argtypes = [ctypes.c_uint64]
+    L.bfc_set_wait_limit.restype = i32
     L.bfc_plan_stats.argtypes = [P, i32, P, P]
     L.bfc_plan_stats.restype = i32
     L.bfc_profile_enable.argtypes = [i32]
@@ -146,6 +148,11 @@ def _dptr(t) -> int:
 def bfc_fail_alloc_after(n: int):
     """Make the library's (n+1)-th next device allocation fail (n < 0: none)."""
     _check(load().bfc_fail_alloc_after(int(n)), "bfc_fail_alloc_after")
+
+
+def bfc_set_wait_limit(ns: int):
+    """Give-up limit (ns of GPU time) of the hub kernel's device waits; 0 = built-in."""
+    _check(load().bfc_set_wait_limit(int(ns)), "bfc_set_wait_limit")
 
 
 def bfc_trim_memory():

@@ -31,7 +31,10 @@ constexpr int KC = 64;           // K elements per chunk (4 MMAs of K = 16)
 constexpr int HB_THREADS = 128;  // one warpgroup
 constexpr int SW = 4;            // tiles per strip: (ti, tj .. tj + 3) share the A_i chunk
 constexpr int HB_PER_SM = 1;     // one CTA per SM: 4 x 128 TMEM columns, 2 x 80 KB of stages
-constexpr uint64_t WAIT_NS = 1000000000ull;  // bounded waits give up after ~1 s
+constexpr uint64_t WAIT_NS = 1000000000ull;   // bounded waits give up after ~1 s
+constexpr uint64_t DRAIN_NS = 2000000000ull;  // after giving up: the wait for work already issued
+// the give-up limit of the next launches (bfc_set_wait_limit; 0: WAIT_NS)
+static uint64_t g_wait_ns = 0;
 constexpr uint32_t OP_BYTES = TM * KC * 2;                 // one 128 x 64 operand chunk, 16 KB
 constexpr uint32_t STAGE_BYTES = (1 + SW) * OP_BYTES;      // A_i and up to four A_j chunks
 constexpr size_t HB_SMEM = 2 * STAGE_BYTES + 1024;         // two stages, plus room to align them to 1 KB
@@ -144,9 +147,9 @@ __device__ __forceinline__ void strip_of(uint32_t t, uint32_t nt, uint32_t &ti, 
   tj0 = i + rem * SW;
 }
 
-// Wait for phase `parity` of an mbarrier for at most about one second of
-// global time; returns 1 when the phase completed.
-__device__ __forceinline__ uint32_t mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+// Wait for phase `parity` of an mbarrier for at most limit_ns of global time;
+// returns 1 when the phase completed.
+__device__ __forceinline__ uint32_t mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
   uint64_t t0;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
   while (true) {
@@ -158,7 +161,7 @@ __device__ __forceinline__ uint32_t mbar_wait_bounded(uint32_t bar, uint32_t par
     if (done) return 1;
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    if (t - t0 > WAIT_NS) return 0;
+    if (t - t0 > limit_ns) return 0;
   }
 }
 
@@ -179,9 +182,12 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
 // commits them to the stage's `empty` barrier, which frees the stage.  After
 // the last chunk a commit to `done` releases the epilogue: the 4 warps read
 // each accumulator (TMEM lane = tile row), add C_L and sum C(c, 2) over i < j.
+// Every wait gives up after wait_ns: the CTA then stops issuing, sets
+// DERR_TIMEOUT, waits (at most DRAIN_NS each) for the copies it issued and
+// for its MMAs, and only then releases its tensor memory and exits.
 __global__ void __launch_bounds__(HB_THREADS) k_hub_mma(const __grid_constant__ CUtensorMap amap, uint32_t Kp,
                                                         uint32_t h, const unsigned int *CL, unsigned int *queue,
-                                                        unsigned long long *B, uint32_t *err) {
+                                                        unsigned long long *B, uint32_t *err, uint64_t wait_ns) {
   extern __shared__ uint8_t hub_smem[];
   __shared__ __align__(8) uint64_t full[2], empty[2], done;
   __shared__ uint32_t tmem_holder, sh_item, sh_ok;
@@ -210,6 +216,8 @@ __global__ void __launch_bounds__(HB_THREADS) k_hub_mma(const __grid_constant__ 
   uint32_t nitems = 0;
   for (uint32_t i = 0; i < nt; i++) nitems += (nt - i + SW - 1) / SW;
   uint32_t q = 0;      // chunks issued so far by this CTA (thread 0): stage q & 1, its use q >> 1
+  uint32_t q_iss = 0;  // chunk copies issued (thread 0)
+  uint32_t q_ful = 0;  // chunk copies waited for (thread 0): those in [q_ful, q_iss) may be in flight
   uint32_t nfin = 0;   // strips finished by this CTA
   unsigned long long acc = 0;
   // copy chunk c of the strip into the stage of chunk number qn
@@ -230,16 +238,24 @@ __global__ void __launch_bounds__(HB_THREADS) k_hub_mma(const __grid_constant__ 
     const uint32_t w = min((uint32_t)SW, nt - tj0);  // tiles in this strip
     if (tid == 0) {
       bool ok = true;
-      if (q >= 2) ok = mbar_wait_bounded(smem_u32(&empty[q & 1]), ((q - 2) >> 1) & 1);
-      if (ok) issue(q, 0, ti, tj0, w);
+      if (q >= 2) ok = mbar_wait_bounded(smem_u32(&empty[q & 1]), ((q - 2) >> 1) & 1, wait_ns);
+      if (ok) {
+        issue(q, 0, ti, tj0, w);
+        q_iss = q + 1;
+      }
       for (uint32_t c = 0; c < nchunks && ok; c++) {
         const uint32_t qc = q + c;
         if (c + 1 < nchunks) {
           const uint32_t qn = qc + 1;  // its stage was last read by chunk qn - 2
-          if (qn >= 2 && !mbar_wait_bounded(smem_u32(&empty[qn & 1]), ((qn - 2) >> 1) & 1)) { ok = false; break; }
+          if (qn >= 2 && !mbar_wait_bounded(smem_u32(&empty[qn & 1]), ((qn - 2) >> 1) & 1, wait_ns)) {
+            ok = false;
+            break;
+          }
           issue(qn, c + 1, ti, tj0, w);
+          q_iss = qn + 1;
         }
-        if (!mbar_wait_bounded(smem_u32(&full[qc & 1]), (qc >> 1) & 1)) { ok = false; break; }
+        if (!mbar_wait_bounded(smem_u32(&full[qc & 1]), (qc >> 1) & 1, wait_ns)) { ok = false; break; }
+        q_ful = qc + 1;
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint32_t stage = st0 + (qc & 1) * STAGE_BYTES;
 #pragma unroll
@@ -266,11 +282,22 @@ __global__ void __launch_bounds__(HB_THREADS) k_hub_mma(const __grid_constant__ 
         atomicOr(err, DERR_TIMEOUT);
       }
     }
-    const uint32_t fin = mbar_wait_bounded(smem_u32(&done), nfin & 1);
+    const uint32_t fin = mbar_wait_bounded(smem_u32(&done), nfin & 1, wait_ns);
     nfin++;
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (__syncthreads_and(fin) == 0 || !sh_ok) {
-      if (tid == 0) { sh_ok = 0; atomicOr(err, DERR_TIMEOUT); }
+      if (tid == 0) {
+        sh_ok = 0;
+        atomicOr(err, DERR_TIMEOUT);
+        // before the shared and tensor memory are released: the copies not
+        // yet waited for (at most one per stage: a stage is refilled only
+        // after its MMAs completed), then every MMA issued (the `done` phase
+        // committed after them)
+        for (uint32_t x = q_ful; x < q_iss; x++) mbar_wait_bounded(smem_u32(&full[x & 1]), (x >> 1) & 1, DRAIN_NS);
+        mbar_wait_bounded(smem_u32(&done), (nfin - 1) & 1, DRAIN_NS);
+        asm volatile("tcgen05.fence::after_thread_sync;");
+      }
+      __syncthreads();
       break;
     }
     // epilogue: row i of each tile is TMEM lane i; sum C(c, 2) over global i < j
@@ -465,7 +492,8 @@ int hub_block_count(bfc_graph *g, Plan &p, uint32_t h, uint32_t tau, unsigned lo
   HB_TRY(hub_tensor_map(&amap, A.p, h, Kp));
   HB_CUDA(cudaFuncSetAttribute(k_hub_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HB_SMEM));
   profile_begin("hub.total", s);
-  k_hub_mma<<<grid, HB_THREADS, HB_SMEM, s>>>(amap, Kp, h, ptr<unsigned int>(CL), queue, d_B, ptr<uint32_t>(g->err));
+  k_hub_mma<<<grid, HB_THREADS, HB_SMEM, s>>>(amap, Kp, h, ptr<unsigned int>(CL), queue, d_B, ptr<uint32_t>(g->err),
+                                              g_wait_ns ? g_wait_ns : WAIT_NS);
   count_launch();
   profile_end("hub.total", s);
   HB_CUDA(cudaGetLastError());
@@ -485,3 +513,8 @@ int hub_block_count(bfc_graph *g, Plan &p, uint32_t h, uint32_t tau, unsigned lo
 }
 
 }  // namespace bfc
+
+extern "C" int bfc_set_wait_limit(uint64_t ns) {
+  bfc::g_wait_ns = ns;
+  return BFC_OK;
+}

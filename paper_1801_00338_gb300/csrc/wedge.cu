@@ -206,7 +206,9 @@ __device__ __forceinline__ uint64_t warp_sum_u64_small(uint64_t x) {
 __device__ __forceinline__ uint32_t wh_hash(uint32_t w) { return (w * 0x9E3779B1u) >> (32 - 10); }
 static_assert(WH_SLOTS == 1024, "wh_hash assumes 1024 slots");
 
-__device__ __forceinline__ void wh_insert(uint32_t *keys, uint32_t *cnts, uint32_t w) {
+// (the class limit keeps a table at most half full, so the probe sequence
+// always ends; a full table would be an internal error, reported, not dropped)
+__device__ __forceinline__ void wh_insert(uint32_t *keys, uint32_t *cnts, uint32_t w, uint32_t *err) {
   uint32_t h = wh_hash(w);
   for (int probe = 0; probe < WH_SLOTS; probe++) {
     uint32_t k = keys[h];
@@ -217,6 +219,7 @@ __device__ __forceinline__ void wh_insert(uint32_t *keys, uint32_t *cnts, uint32
     }
     h = (h + 1) & (WH_SLOTS - 1);
   }
+  atomicOr(err, DERR_CAPACITY);
 }
 __device__ __forceinline__ uint32_t wh_lookup(const uint32_t *keys, const uint32_t *cnts, uint32_t w) {
   uint32_t h = wh_hash(w);
@@ -284,7 +287,7 @@ __global__ void __launch_bounds__(WH_WARPS * 32) k_warp_class(WArgs a) {
     const uint64_t rb = a.offR[r], re = (r < a.rank_end) ? a.offR[r + 1] : rb;  // ranks >= rank_end: done elsewhere
     warp_for_each_wedge<Full<MODE>::value>(a, rb, re, [&](uint32_t i, uint64_t) {
       const uint32_t w = a.mR[i];
-      if (!Full<MODE>::value || w != r) wh_insert(keys, cnts, w);
+      if (!Full<MODE>::value || w != r) wh_insert(keys, cnts, w, a.err);
     });
     __syncwarp();
     if (MODE == MODE_EDGE) {

@@ -115,3 +115,26 @@ def test_batched_exact(bfc):
     for (u, v, nU, nV), b, sd in zip(graphs, B, side):
         ob, os_ = O.exact(u, v, nU, nV)
         assert int(b) == ob and int(sd) == os_
+
+
+ETIMEOUT = -6
+
+
+def test_hub_wait_gives_up_and_the_handle_recovers(bfc, medium):
+    """The hub kernel's bounded waits: with a 1 ns limit the first wait for a
+    TMA copy gives up (the copy cannot land that fast), the kernel drains what
+    it issued and the call returns BFC_ETIMEOUT; with the limit restored the
+    same handle gives the oracle's count, repeatedly."""
+    g, oB, _ = medium
+    with bfc.Graph(g.u, g.v, g.nU, g.nV) as G:
+        try:
+            bfc.bfc_set_wait_limit(1)
+            with pytest.raises(bfc.BfcError) as ei:
+                G.exact_hub(hubs=256, tau=2)
+            assert ei.value.code == ETIMEOUT
+        finally:
+            bfc.bfc_set_wait_limit(0)
+        for _ in range(2):
+            B, _, st = G.exact_hub(hubs=256, tau=2)
+            assert B == oB and st["hubs"] == 256
+        assert G.exact()[0] == oB
