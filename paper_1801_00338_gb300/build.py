@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libbfc.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["primitives.cu", "graph.cu", "wedge.cu", "estimators.cu", "vsamp.cu", "capi.cu", "noalloc.cu", "batch.cu", "mlp.cu", "hub.cu", "samplers.cu"]
+SOURCES = ["primitives.cu", "graph.cu", "wedge.cu", "estimators.cu", "vsamp.cu", "capi.cu", "noalloc.cu", "batch.cu", "mlp.cu", "hub.cu", "samplers.cu", "trials.cu"]
 
 
 def _nvcc() -> str:

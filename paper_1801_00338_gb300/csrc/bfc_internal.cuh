@@ -181,13 +181,10 @@ int wedge_count(bfc_graph *g, Plan &p, Mode mode, unsigned long long *d_B, uint6
 int wedge_count_groups(bfc_graph *g, Plan &p, const uint32_t *grp_of_rank, unsigned long long *gB,
                        unsigned long long *d_B, cudaStream_t s);
 int plan_classify(bfc_graph *g, Plan &p, cudaStream_t s);
-// The same classification with counts, offsets and lists left on the device
-// (dev: 48 words; sums: 2 NCLS + 1 u64 of scratch), and TOTAL counting that
-// reads them there: no host round trip, so both can be recorded in a graph.
-int plan_classify_device(Plan &p, uint32_t *cls_of, unsigned int *dev, unsigned long long *sums, cudaStream_t s);
-int wedge_count_device_lists(bfc_graph *g, Plan &p, const unsigned int *dev, uint32_t big_cap,
-                             unsigned long long *d_B, cudaStream_t s);
-void plan_free(Plan &p, cudaStream_t s);
+// ESpar (kind 0, keep threshold thr) or ClrSpar (kind 1, colors) trials
+// 0 .. trials - 1 of the sequence seeded by seed; beta: host (trials.cu)
+int run_trials(bfc_graph *g, int kind, uint64_t seed, uint32_t thr, uint32_t colors, uint32_t trials, uint64_t *beta,
+               cudaStream_t s);
 // b_x = 1/2 sum of b_e over the rows off[x] .. off[x+1] (Lemma 1's identity
 // for one vertex); eid: canonical id of each row entry, or null for identity.
 int vertex_from_edges(const uint64_t *off, uint32_t n, const uint32_t *eid, const uint64_t *be, uint64_t *out,

@@ -154,23 +154,12 @@ struct WArgs {
   // also goes to gB[grp[rank]] (its graph's count)
   const uint32_t *grp;
   unsigned long long *gB;
-  // class lists whose lengths live on the device (launches recorded before
-  // the counts are known): list = dev_lists + dev_begin[cls], list_n = dev_count[cls]
-  const uint32_t *dev_lists;
-  const unsigned int *dev_begin, *dev_count;
   uint32_t cls;
   // start ranks >= rank_end walk nothing (their pairs are counted by the
   // hub block); nS otherwise
   uint32_t rank_end;
 };
 
-// resolve the vertex list of a launch (host-known or device-resident)
-__device__ __forceinline__ void resolve_list(WArgs &a) {
-  if (a.dev_count) {
-    a.list = a.dev_lists + a.dev_begin[a.cls];
-    a.list_n = a.dev_count[a.cls];
-  }
-}
 
 __device__ __forceinline__ uint64_t umin64(uint64_t x, uint64_t y) { return x < y ? x : y; }
 __device__ __forceinline__ uint32_t umax32(uint32_t x, uint32_t y) { return x > y ? x : y; }
@@ -270,7 +259,6 @@ __device__ __forceinline__ void warp_for_each_wedge(const WArgs &a, uint64_t rb,
 template <int MODE>
 __global__ void __launch_bounds__(WH_WARPS * 32) k_warp_class(WArgs a) {
   extern __shared__ uint32_t smem[];
-  resolve_list(a);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t *keys = smem + (size_t)warp * 2 * WH_SLOTS;
   uint32_t *cnts = keys + WH_SLOTS;
@@ -778,13 +766,15 @@ __device__ __forceinline__ bool count_hl(const WArgs &a, uint64_t rb, uint64_t r
   return true;
 }
 
+// (the whole-row modes, off the default path, are compiled for two fewer resident
+// CTAs: their read sweep needs a few more registers than the 42 that twelve
+// 128-thread CTAs leave)
 template <int MODE, int CW, int P>
-__global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win(WArgs a) {
+__global__ void __launch_bounds__(WinCfg<P>::THREADS, (Full<MODE>::value && WinCfg<P>::MINB > 4) ? WinCfg<P>::MINB - 2 : WinCfg<P>::MINB) k_cta_win(WArgs a) {
   constexpr int WIN_THREADS = WinCfg<P>::THREADS;
   constexpr uint32_t WIN_WORDS = WinCfg<P>::WORDS;
   constexpr uint32_t WIN_SMAX = WinCfg<P>::SMAX;
   using C = Ctr<CW, WIN_WORDS>;
-  resolve_list(a);
   extern __shared__ uint32_t sm[];
   uint32_t *ctr = sm;
   uint32_t *s_cur = sm + WIN_WORDS, *s_end = s_cur + WIN_SMAX, *s_ps = s_end + WIN_SMAX, *s_nx = s_ps + WIN_SMAX;
@@ -1021,7 +1011,6 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, WinCfg<P>::MINB) k_cta_win
 // ---------------------------------------------------------------------------
 template <int MODE>
 __global__ void __launch_bounds__(CT_THREADS, 1) k_cta_big(WArgs a) {
-  resolve_list(a);
   extern __shared__ uint32_t ctr[];  // BIG_Z counters, then 32 u64 per warp (count_flat's row sums)
   unsigned long long *rs_all = reinterpret_cast<unsigned long long *>(ctr + BIG_Z);
   __shared__ uint32_t s_idx, s_next_min, s_carry;
@@ -1341,28 +1330,23 @@ static const char *tag_of(int kind, int mode) {
   return tags[kind][mode];
 }
 
-// class lists: lists[c], counts[c] for c in [0, NCLS).  With counts == null
-// the lists and their lengths are on the device (a.dev_*): every non-skip class
-// is launched with a full persistent grid and reads its length at start.
+// class lists: lists[c], counts[c] for c in [0, NCLS).
 template <int MODE>
 static int launch_lists(bfc_graph *g, WArgs a, const uint32_t *const *lists, const uint32_t *counts, uint32_t big_cap,
                         cudaStream_t s) {
   const int sms = sm_count();
-  const bool dev = counts == nullptr;
   unsigned int *queues = ptr<unsigned int>(g->acc) + 16;  // one counter per class
   static_assert(64 + 4 * Plan::NCLS <= 256, "queues live in the 256-byte accumulator block");
   BFC_CUDA_TRY(cudaMemsetAsync(queues, 0, 4 * Plan::NCLS, s));
-  auto have = [&](int c) { return dev || counts[c] != 0; };
+  auto have = [&](int c) { return counts[c] != 0; };
   auto setup = [&](WArgs &w, int c) {
     w.cls = (uint32_t)c;
     w.queue = queues + c;
-    if (!dev) {
-      w.list = lists[c];
-      w.list_n = counts[c];
-    }
+    w.list = lists[c];
+    w.list_n = counts[c];
   };
   auto cap = [&](unsigned full, int c) -> unsigned {
-    return dev ? full : std::max(1u, std::min<unsigned>(full, counts[c]));
+    return std::max(1u, std::min<unsigned>(full, counts[c]));
   };
   if (have(CLS_WARP)) {
     WArgs w = a;
@@ -1372,7 +1356,7 @@ static int launch_lists(bfc_graph *g, WArgs a, const uint32_t *const *lists, con
     int occ = 0;
     BFC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_warp_class<MODE>, WH_WARPS * 32, smem));
     const unsigned full = (unsigned)std::max(1, occ) * sms;
-    const unsigned grid = dev ? full : std::min<unsigned>(full, (counts[CLS_WARP] + WH_WARPS - 1) / WH_WARPS);
+    const unsigned grid = std::min<unsigned>(full, (counts[CLS_WARP] + WH_WARPS - 1) / WH_WARPS);
     profile_begin(tag_of(0, MODE), s);
     k_warp_class<MODE><<<grid, WH_WARPS * 32, smem, s>>>(w);
     BFC_LAUNCHED();
@@ -1618,44 +1602,8 @@ __global__ void k_finish_edges(const uint32_t *mEid, uint64_t m, const unsigned 
 }
 
 // ---------------------------------------------------------------------------
-// classification and counting without host round trips (recordable into a
-// CUDA graph): dev = 48 words: counts[16], begin[16], cursor[16]
+// counting entry points
 // ---------------------------------------------------------------------------
-__global__ void k_cls_offsets(unsigned int *dev) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    unsigned int run = 0;
-    for (int c = 0; c < Plan::NCLS; c++) {
-      dev[16 + c] = run;
-      run += dev[c];
-      dev[32 + c] = 0;
-    }
-  }
-}
-
-int plan_classify_device(Plan &p, uint32_t *cls_of, unsigned int *dev, unsigned long long *sums, cudaStream_t s) {
-  BFC_CUDA_TRY(cudaMemsetAsync(dev, 0, 48 * 4, s));
-  k_classify<<<grid_for(p.nS, 256), 256, 0, s>>>(ptr<uint64_t>(p.offR), ptr<uint64_t>(p.work), p.nS, limits_of(p),
-                                                cls_of, dev,
-                                                sums + 2 * Plan::NCLS, sums);
-  count_launch();
-  k_cls_offsets<<<1, 32, 0, s>>>(dev);
-  count_launch();
-  k_scatter_class<<<grid_for(p.nS, 256), 256, 0, s>>>(cls_of, p.nS, dev + 16, dev + 32, ptr<uint32_t>(p.cls));
-  count_launch();
-  BFC_CUDA_TRY(cudaGetLastError());
-  return BFC_OK;
-}
-
-int wedge_count_device_lists(bfc_graph *g, Plan &p, const unsigned int *dev, uint32_t big_cap,
-                             unsigned long long *d_B, cudaStream_t s) {
-  WArgs a = args_of(g, p);
-  a.B = d_B;
-  a.dev_lists = ptr<uint32_t>(p.cls);
-  a.dev_count = dev;
-  a.dev_begin = dev + 16;
-  return launch_lists<MODE_TOTAL>(g, a, nullptr, nullptr, big_cap, s);
-}
-
 int wedge_count_groups(bfc_graph *g, Plan &p, const uint32_t *grp_of_rank, unsigned long long *gB,
                        unsigned long long *d_B, cudaStream_t s) {
   WArgs a = args_of(g, p);

@@ -222,3 +222,31 @@ def uneven_batch_params(count: int, seed: int, m_lo: float = 1e3, m_hi: float = 
             nV += 1
         out.append((nU, nV, m, gamma))
     return out
+
+
+def uneven_batch_graph(i: int, params) -> tuple[np.ndarray, np.ndarray, int, int]:
+    """Graph i of a batch made by uneven_batch_params: a Chung-Lu graph with
+    the same exponent on both sides, seed 100,000 + i."""
+    nU, nV, m, gamma = params[i]
+    u, v = chung_lu_bipartite(nU, nV, m, gamma, gamma, 100_000 + i)
+    return u, v, nU, nV
+
+
+def _batch_graph_job(args):
+    i, params = args
+    return uneven_batch_graph(i, params)
+
+
+def uneven_batch(count: int, seed: int, workers: int = 0, m_lo: float = 1e3, m_hi: float = 1e6):
+    """The graphs of uneven_batch_params(count, seed, m_lo, m_hi) as (u, v, nU,
+    nV) tuples, made by a pool of spawned worker processes (none inherits a
+    CUDA context); the graphs do not depend on the worker count."""
+    import multiprocessing as mp
+    import os
+    params = uneven_batch_params(count, seed, m_lo, m_hi)
+    jobs = [(i, params) for i in range(count)]
+    workers = workers or min(16, os.cpu_count() or 1)
+    if workers <= 1:
+        return [_batch_graph_job(j) for j in jobs]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(_batch_graph_job, jobs, chunksize=8)

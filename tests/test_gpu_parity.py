@@ -211,6 +211,37 @@ def test_clrspar_trials_match_oracle(bfc, side_stream):
         assert est[t] == oe
 
 
+@pytest.mark.parametrize("side_stream", [False, True])
+def test_many_sparse_trials_match_oracle(bfc, side_stream):
+    """70 ESpar trials at p = 0.05 and 70 ClrSpar trials with 20 colours (the
+    batched estimators' settings), trial by trial: the persistent launch takes
+    its work in chunks of 32 trials, so 70 spans a ragged third chunk; on a
+    side stream the launches are recorded into one CUDA graph."""
+    import torch
+    g = synth.chung_lu_scaled(20_000, 40_000, 300_000, 2.0, 2.3, 3)
+    st = torch.cuda.Stream() if side_stream else None
+    with bfc.Graph(g.u, g.v, g.nU, g.nV) as G:
+        _, beta = G.espar(0.05, 70, 2024, stream=st)
+        _, beta2 = G.clrspar(20, 70, 2025, stream=st)
+    for t in range(70):
+        assert int(beta[t]) == O.espar_trial(g.u, g.v, g.nU, g.nV, 0.05, 2024, t)[0], t
+        assert int(beta2[t]) == O.clrspar_trial(g.u, g.v, g.nU, g.nV, 20, 2025, t)[0], t
+
+
+def test_dense_trials_take_the_heavy_path(bfc):
+    """Keep probability 0.9 on a skewed graph: most (start vertex, trial) pairs
+    overflow the per-warp tables and are counted from the heavy list by whole
+    CTAs with global tables; every trial still equals the oracle's."""
+    g = synth.chung_lu_scaled(30_000, 8_000, 200_000, 2.1, 2.5, 41)
+    with bfc.Graph(g.u, g.v, g.nU, g.nV) as G:
+        _, beta = G.espar(0.9, 5, 555)
+        _, beta2 = G.clrspar(1, 2, 556)
+    B = O.exact(g.u, g.v, g.nU, g.nV)[0]
+    for t in range(5):
+        assert int(beta[t]) == O.espar_trial(g.u, g.v, g.nU, g.nV, 0.9, 555, t)[0], t
+    assert [int(b) for b in beta2] == [B, B]  # one colour keeps every edge
+
+
 def _vsamp_check(bfc, g, k, trials, seed, weights=None):
     import torch
     with bfc.Graph(g.u, g.v, g.nU, g.nV) as G:
