@@ -270,6 +270,145 @@ def run_reference(args, rank, world):
 
 
 # ----------------------------------------------------------------------------
+# the other workloads of the line (untimed by the step; each reports its own
+# times, measured around whole library calls)
+# ----------------------------------------------------------------------------
+
+def extra_batch(bfc) -> dict:
+    """Batched exact counting of 4,096 seeded uneven graphs (m log-uniform in
+    [10^3, 10^6], side ratio in [0.2, 5], exponent in [1.9, 3.0]) in one
+    bfc_exact_batch call: host edge lists in, per-graph B and side out."""
+    import torch
+    from paper_1801_00338_gb300 import synth
+    t0 = time.perf_counter()
+    graphs = synth.uneven_batch(4096, 5)
+    gen_s = time.perf_counter() - t0
+    edges, W = 0, 0
+    for u, v, nU, nV in graphs:
+        dU = np.bincount(u, minlength=nU).astype(np.float64)
+        dV = np.bincount(v, minlength=nV).astype(np.float64)
+        mid = dU if (dU * dU).sum() < (dV * dV).sum() else dV  # Algorithm 1: wedges centred on the other side
+        W += int((mid * (mid - 1) / 2).sum())
+        edges += len(u)
+    bfc.bfc_exact_batch(graphs)  # warm-up
+    times = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B, side = bfc.bfc_exact_batch(graphs)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    dt = float(np.median(times))
+    return {"workload": "4096 uneven Chung-Lu graphs, synth.uneven_batch_params(4096, 5)", "graphs": 4096,
+            "edges": edges, "W": W, "gen_s": gen_s, "s_per_call": dt, "s_all": times, "graphs_per_s": 4096 / dt,
+            "edges_per_s": edges / dt, "wedges_per_s": W / dt, "B_total": int(B.astype(np.float64).sum()),
+            "h2d_in_timed_call": True}
+
+
+def extra_estimators(bfc) -> dict:
+    """256 ESpar trials at p = 0.05 and 256 ClrSpar trials with 20 colours
+    (each estimator one persistent launch) on the 20M x 40M, 300M-edge
+    Chung-Lu graph (exponents 2.0 / 2.3, seed 3), against its exact count."""
+    import torch
+    from paper_1801_00338_gb300 import synth
+    t0 = time.perf_counter()
+    g = synth.chung_lu_scaled(20_000_000, 40_000_000, 300_000_000, 2.0, 2.3, 3)
+    out = {"workload": "chung_lu_U20M_V40M_E300M_g2.0_2.3_seed3", "gen_s": time.perf_counter() - t0}
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        G = bfc.Graph(g.u, g.v, g.nU, g.nV, stream=stream)
+    del g
+    try:
+        B, side = G.exact(stream=stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B2, _ = G.exact(stream=stream)
+        torch.cuda.synchronize()
+        out["exact"] = {"B": int(B), "start_side": "UV"[side], "s": time.perf_counter() - t0}
+        assert B2 == B
+        st = G.stats
+        out["exact"]["W"] = int(st["wedges_v"] if side == 0 else st["wedges_u"])
+        out["exact"]["wedges_per_s"] = out["exact"]["W"] / out["exact"]["s"]
+        # scheduling settings chosen by the autotuner for this graph's exact count
+        from paper_1801_00338_gb300 import autotune as AT
+        res = AT.autotune(G, ("exact",), use_cache=False)
+        assert res.counts[0] == B
+        out["tuning"] = dict(res.tuning, source="autotuner (" + res.source + ")", tuned_ms=res.ms,
+                             default_ms=res.default_ms, candidates_timed=len(res.tried))
+        for name, fn, arg in (("espar", G.espar, 0.05), ("clrspar", G.clrspar, 20)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            est, _ = fn(arg, 256, 2024, stream=stream)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            est = np.asarray(est, np.float64)
+            rel = np.abs(est - B) / B
+            out[name] = {("p" if name == "espar" else "colors"): arg, "trials": 256, "launches_per_call": 1,
+                         "mean": float(est.mean()), "median": float(np.median(est)),
+                         "rel_err_of_mean": float(abs(est.mean() - B) / B),
+                         "median_rel_err_single": float(np.median(rel)), "s_total": dt, "ms_per_trial": dt / 256 * 1e3}
+    finally:
+        G.close()
+    return out
+
+
+def extra_vsamp(bfc) -> dict:
+    """The learned proposal: trained on 200 seeded Chung-Lu graphs (m
+    log-uniform in [10^5, 2 x 10^7]), then uniform against learned VSamp at
+    equal GPU time on the held-out 5M x 10M, 100M-edge graph."""
+    import torch
+    from paper_1801_00338_gb300 import learned as Ln
+    from paper_1801_00338_gb300 import synth
+    tr, info = Ln.train_proposal(count=200, m_lo=1e5, m_hi=2e7, steps=2000, seed=0)
+    t0 = time.perf_counter()
+    h = synth.chung_lu_scaled(5_000_000, 10_000_000, 100_000_000, 2.3, 2.3, 10_000)
+    info["heldout_gen_s"] = time.perf_counter() - t0
+    with bfc.Graph(h.u, h.v, h.nU, h.nV) as G:
+        del h
+        bU, bV, B = G.per_vertex()
+        b = np.concatenate([bU.cpu().numpy(), bV.cpu().numpy()]).astype(np.float64)
+        res = Ln.equal_time(G, b, int(B), tr.wb, trials=3, seed=7)
+    res["training"] = info
+    res["heldout"] = {"workload": "chung_lu_U5M_V10M_E100M_g2.3_2.3_seed10000", "B": int(B)}
+    return res
+
+
+def run_profile_case(scale: int):
+    """The benchmark's graph shrunk by `scale` (|U| = 10^6 / S, |V| = 5 x 10^6 / S,
+    5 x 10^7 / S edges, the same exponents and seed): graph build,
+    bfc_exact(BFC_HUB_MMA) and bfc_local_counts twice, for profilers."""
+    import ctypes
+
+    import torch
+
+    from paper_1801_00338_gb300 import bfc, synth
+    from paper_1801_00338_gb300 import build as B
+    B.build()
+    S = scale
+    g = synth.chung_lu_scaled(1_000_000 // S, 5_000_000 // S, 50_000_000 // S, 2.1, 2.5, 2)
+    du = torch.from_numpy(g.u.astype(np.int32)).cuda()
+    dv = torch.from_numpy(g.v.astype(np.int32)).cuda()
+    bU = torch.empty(g.nU, dtype=torch.int64, device="cuda")
+    bV = torch.empty(g.nV, dtype=torch.int64, device="cuda")
+    be = torch.empty(g.m, dtype=torch.int64, device="cuda")
+    L = bfc.load()
+    sp = torch.cuda.current_stream().cuda_stream
+    Bv, B2, side = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int()
+    for _ in range(2):
+        h = bfc.bfc_graph_from_edges(du, dv, g.nU, g.nV, 0, sp)
+        try:
+            bfc._check(L.bfc_exact(h, bfc.BFC_HUB_MMA, ctypes.byref(Bv), ctypes.byref(side), sp), "bfc_exact")
+            bfc._check(L.bfc_local_counts(h, 0, bU.data_ptr(), bV.data_ptr(), be.data_ptr(), ctypes.byref(B2), sp),
+                       "bfc_local_counts")
+        finally:
+            bfc.bfc_graph_free(h)
+    torch.cuda.synchronize()
+    assert Bv.value == B2.value
+    print(f"profile case 1/{S}: |U|={g.nU} |V|={g.nV} m={g.m} B={Bv.value}")
+    return 0
+
+
+# ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
 
@@ -472,6 +611,18 @@ def run_own(args, rank, world, local_rank):
                                                      "kind": "oracle", "sample": desca}
             except Exception as e:  # noqa: BLE001
                 line["cpu_baseline"]["all_cores"] = {"unavailable": f"{type(e).__name__}: {e}"[:200]}
+    if rank == 0 and args.extras:
+        # the other workloads (each failure is reported in its key, the line stands)
+        del du, dv, bU, bV, be, hu, hv, obU, obV, obe
+        torch.cuda.empty_cache()
+        for key, fn in (("batch", extra_batch), ("estimators", extra_estimators), ("vsamp_equal_time", extra_vsamp)):
+            t0 = time.perf_counter()
+            try:
+                line[key] = fn(bfc)
+            except Exception as e:  # noqa: BLE001
+                line[key] = {"unavailable": f"{type(e).__name__}: {e}"[:300]}
+            line[key]["wall_s"] = time.perf_counter() - t0
+            print(f"{key}: {time.perf_counter() - t0:.0f} s", file=sys.stderr, flush=True)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -490,12 +641,18 @@ def main():
     ap.add_argument("--cpu-all-cores", action=argparse.BooleanOptionalAction, default=True,
                     help="also time the oracle on every host core (spawned processes)")
     ap.add_argument("--no-autotune", action="store_true", help="count with the default scheduling settings")
+    ap.add_argument("--extras", action=argparse.BooleanOptionalAction, default=True,
+                    help="also run the batched-graph, sparsification-estimator and learned-VSamp workloads")
+    ap.add_argument("--profile-case", type=int, default=0, metavar="S",
+                    help="only run the benchmark graph shrunk by S twice (for profilers) and exit")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.profile_case:
+        return run_profile_case(args.profile_case)
     if args.impl == "reference":
         return run_reference(args, rank, world)
     return run_own(args, rank, world, local_rank)

@@ -207,6 +207,103 @@ def time_vsamp(G: "bfc.Graph", k: int, trials: int, seed: int, prop=None, reps: 
     return (time.perf_counter() - t0) / reps
 
 
+def _train_graph_job(args):
+    i, (nU, nV, m, gu, gv), seed = args
+    u, v = synth.chung_lu_bipartite(nU, nV, m, gu, gv, seed)
+    return u, v, nU, nV
+
+
+def train_proposal(count: int = 200, m_lo: float = 1e5, m_hi: float = 2e7, steps: int = 2000, seed: int = 0,
+                   workers: int = 0):
+    """Train the proposal network: `count` Chung-Lu graphs with m log-uniform in
+    [m_lo, m_hi] and exponents uniform in [1.9, 2.8] (generated by spawned
+    worker processes), exact per-vertex labels from the library, `steps` Adam
+    steps of 65,536 rows.  Returns (trainer, info)."""
+    import multiprocessing as mp
+    import os
+    import torch
+    info = {"train_graphs": count, "train_m_range": [m_lo, m_hi], "steps": steps}
+    t0 = time.perf_counter()
+    params = training_graph_params(count, seed + 21, m_lo, m_hi)
+    jobs = [(i, prm, 10_000 + seed * 1000 + i) for i, prm in enumerate(params)]
+    workers = workers or min(16, os.cpu_count() or 1)
+    with mp.get_context("spawn").Pool(workers) as pool:
+        graphs = pool.map(_train_graph_job, jobs, chunksize=2)
+    info["train_edges"] = int(sum(len(g[0]) for g in graphs))
+    info["gen_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    data = dataset_from_graphs(graphs)
+    del graphs
+    torch.cuda.synchronize()
+    info["label_s"] = time.perf_counter() - t0
+    tr = Trainer(seed=seed, lr=3e-3, out_bias=float(data.T.mean().item()))
+    info["mse_before"] = tr.mse(data)
+    t0 = time.perf_counter()
+    tr.fit(data, steps=steps, batch=65536)
+    torch.cuda.synchronize()
+    info["train_s"] = time.perf_counter() - t0
+    info["mse_after"] = tr.mse(data)
+    return tr, info
+
+
+def equal_time(G: "bfc.Graph", b: np.ndarray, B: int, wb, trials: int = 3, seed: int = 0, rel: float = 0.01) -> dict:
+    """Uniform against learned VSamp (Algorithm 4; the learned mixture reweighted
+    by Horvitz-Thompson) at equal GPU time on one graph: the learned arm runs
+    the draws its exact variance predicts for a `rel` median error, its time
+    including the proposal build (features, network, weights, prefix table);
+    the uniform arm then gets the same time per trial.  Both arms' median
+    relative errors over `trials` trials are measured."""
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    prop = proposal(G, wb)
+    torch.cuda.synchronize()
+    t_prop = time.perf_counter() - t0
+    try:
+        n = G.nU + G.nV
+        q = mixture_q(prop, n)
+        var_u = single_draw_variance(b)
+        var_l = single_draw_variance(b, q)
+        k_l = draws_for_median_error(var_l, B, rel)
+        k_u_pred = draws_for_median_error(var_u, B, rel)
+        G.vsamp(1024, 2, seed + 99, proposal=prop)  # warm-up of both sides' layouts
+        G.vsamp(1024, 2, seed + 98)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        est_l = G.vsamp(k_l, trials, seed + 1, proposal=prop)
+        torch.cuda.synchronize()
+        t_l = (time.perf_counter() - t0) / trials + t_prop
+        # uniform: a call's fixed cost and per-draw time from two pilots, then
+        # the draws that fill t_l
+        pilot = []
+        for kp in (1 << 20, 1 << 22):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            G.vsamp(kp, 1, seed + 2)
+            torch.cuda.synchronize()
+            pilot.append((kp, time.perf_counter() - t0))
+        t_draw_u = max((pilot[1][1] - pilot[0][1]) / (pilot[1][0] - pilot[0][0]), 1e-12)
+        t_fixed = max(0.0, pilot[0][1] - pilot[0][0] * t_draw_u)
+        k_u = max(1, int((t_l - t_fixed) / t_draw_u))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        est_u = G.vsamp(k_u, trials, seed + 3)
+        torch.cuda.synchronize()
+        t_u = (time.perf_counter() - t0) / trials
+    finally:
+        bfc.bfc_proposal_free(prop)
+    err_l = np.abs(np.asarray(est_l, np.float64) - B) / B
+    err_u = np.abs(np.asarray(est_u, np.float64) - B) / B
+    return {"trials": trials, "target_rel_err": rel,
+            "learned": {"draws": int(k_l), "s_per_trial": t_l, "proposal_build_s": t_prop,
+                        "median_rel_err": float(np.median(err_l)), "var_single_draw": var_l},
+            "uniform": {"draws": int(k_u), "s_per_trial": t_u, "median_rel_err": float(np.median(err_u)),
+                        "var_single_draw": var_u, "draws_for_target": int(k_u_pred),
+                        "s_for_target": k_u_pred * t_draw_u},
+            "time_ratio_to_target": t_l / (k_u_pred * t_draw_u),
+            "error_ratio_at_equal_time": float(np.median(err_l) / max(np.median(err_u), 1e-300))}
+
+
 def evaluate(train_count: int = 200, m_lo: float = 1e4, m_hi: float = 1e6, steps: int = 2000,
              heldout=(5_000_000, 10_000_000, 100_000_000, 2.3, 2.3, 10_000), k_timing: int = 4096,
              trials_check: int = 30, seed: int = 0, check_budget_s: float = 60.0) -> dict:

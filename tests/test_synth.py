@@ -38,11 +38,14 @@ def test_uneven_batch_params():
 
 
 def test_batch_generation_does_not_depend_on_the_worker_count():
-    """The batched workload's graphs (and W) come out the same whether they are
-    drawn in one process or by a pool of spawned workers."""
-    from paper_1801_00338_gb300 import batch_eval
-    g1, W1 = batch_eval.generate(12, 5, 1e3, 2e4, workers=1)
-    g2, W2 = batch_eval.generate(12, 5, 1e3, 2e4, workers=2)
-    assert W1 == W2 and len(g1) == len(g2) == 12
+    """The batched workload's graphs come out the same whether they are drawn
+    in one process or by a pool of spawned workers, and graph i is
+    uneven_batch_graph(i, params)."""
+    g1 = synth.uneven_batch(12, 5, workers=1, m_hi=2e4)
+    g2 = synth.uneven_batch(12, 5, workers=2, m_hi=2e4)
+    assert len(g1) == len(g2) == 12
     for a, b in zip(g1, g2):
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and a[2:] == b[2:]
+    params = synth.uneven_batch_params(12, 5, m_hi=2e4)
+    u, v, nU, nV = synth.uneven_batch_graph(7, params)
+    assert np.array_equal(u, g1[7][0]) and (nU, nV) == g1[7][2:]
