@@ -434,10 +434,9 @@ int bfc_get_tuning(const bfc_graph *g, bfc_tuning *t);
 
 /* B(G) of a graph given as device CSR arrays, without allocating anything.
  * For callers that cannot allocate device memory when they need the count:
- * work recorded while a stream is being captured (cudaMalloc cannot be
- * recorded into a graph), services whose device memory is reserved up front
- * by another allocator or a fixed budget, and latency-bound loops that must
- * not wait on the allocator.
+ * services whose device memory is reserved up front by another allocator or
+ * held to a fixed budget (an allocation could fail or take memory they do not
+ * own), and latency-bound loops that must not wait on the allocator.
  *   offU : device, nU + 1 row offsets of the U rows;  nbrU : device, V ids
  *   offV : device, nV + 1 row offsets of the V rows;  nbrV : device, U ids
  *          (both sides describe the same simple graph; rows need not be sorted)

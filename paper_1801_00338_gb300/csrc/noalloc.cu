@@ -1,10 +1,9 @@
 // An ExactBFC entry point that allocates no memory.
 //
 // Some callers cannot allocate device memory at the moment they need a count:
-// code that runs while a CUDA stream is being captured (cudaMalloc is not a
-// stream operation and cannot be recorded into a graph), services whose
-// device memory is reserved up front by another allocator or a fixed budget,
-// and latency-bound loops that must not block on the allocator.  For them,
+// services whose device memory is reserved up front by another allocator or
+// held to a fixed budget, and latency-bound loops that must not block on the
+// allocator.  For them,
 // bfc_exact_csr_noalloc counts butterflies of a graph the caller already holds
 // as device CSR arrays, using only a scratch array that is part of this
 // library's image: a file-scope __device__ array of BFC_NOALLOC_SCRATCH_WORDS

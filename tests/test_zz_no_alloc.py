@@ -1,6 +1,6 @@
 """bfc_exact_csr_noalloc: the exact count for callers that cannot allocate
-device memory (inside a stream capture, under a fixed memory budget, on a
-path that must not wait on the allocator).  Its only working memory is a
+device memory (under a fixed memory budget, on a path that must not wait on
+the allocator).  Its only working memory is a
 scratch array inside the library.  Checked against bfc_exact on the same
 edges, on two calls in a row, so that the shared scratch array is seen to be
 reset between calls.
@@ -66,3 +66,24 @@ def test_noalloc_rejects_sizes_beyond_the_scratch(bfc):
                                                z.data_ptr(), None)
     assert too_big == -2  # BFC_ERANGE, before any pointer is touched
     assert bfc.bfc_exact_csr_noalloc(z, z, 3, z, z, 3, z, flags=0x30) == -1  # both sides forced: BFC_EINVAL
+
+
+def test_noalloc_makes_no_library_allocation(bfc):
+    """With the library's next device allocation set to fail, the call still
+    succeeds (it never asks the library's allocator for memory) and gives
+    bfc_exact's count."""
+    import torch
+    g = synth.chung_lu_scaled(3000, 9000, 40_000, 2.1, 2.4, 5)
+    offU, nbrU = _device_csr(g.u, g.v, g.nU)
+    offV, nbrV = _device_csr(g.v, g.u, g.nV)
+    with bfc.Graph(g.u, g.v, g.nU, g.nV) as G:
+        want, _ = G.exact()
+    out = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+    try:
+        bfc.bfc_fail_alloc_after(0)
+        rc = bfc.bfc_exact_csr_noalloc(offU, nbrU, g.nU, offV, nbrV, g.nV, out, 0)
+    finally:
+        bfc.bfc_fail_alloc_after(-1)
+    assert rc == 0, bfc.strerror(rc)
+    torch.cuda.synchronize()
+    assert int(out.item()) == want
