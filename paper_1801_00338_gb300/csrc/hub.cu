@@ -29,7 +29,7 @@ namespace {
 constexpr int TM = 128;          // tile rows / columns
 constexpr int KC = 64;           // K elements per chunk (4 MMAs of K = 16)
 constexpr int HB_THREADS = 128;  // one warpgroup
-constexpr int SW = 4;            // tiles per strip: (ti, tj .. tj + 3) share the A_i chunk
+constexpr int SW = 4;            // tiles per strip at most: (ti, tj .. tj + 3) share the A_i chunk
 constexpr int HB_PER_SM = 1;     // one CTA per SM: 4 x 128 TMEM columns, 2 x 80 KB of stages
 constexpr uint64_t WAIT_NS = 1000000000ull;   // bounded waits give up after ~1 s
 constexpr uint64_t DRAIN_NS = 2000000000ull;  // after giving up: the wait for work already issued
@@ -113,7 +113,7 @@ __global__ void k_fill_dense(const uint64_t *offM, const uint32_t *mR, const uin
   }
 }
 
-// light columns: every hub pair (a < b) of the column adds one to C_L[a][b]
+// light columns: every hub pair (a < b) of the column adds one to C_L[b][a]
 // (one warp per column: the first hub in turn, lanes over the second)
 __global__ void k_light_pairs(const uint64_t *offM, const uint32_t *mR, const uint32_t *hd, uint32_t nM,
                               uint32_t tau, uint32_t hub0, uint32_t h, unsigned int *CL,
@@ -128,8 +128,8 @@ __global__ void k_light_pairs(const uint64_t *offM, const uint32_t *mR, const ui
     const uint64_t e = offM[x + 1], b = e - d;  // the d hubs, ascending ranks
     mine += (uint64_t)d * (d - 1) / 2;
     for (uint32_t i = 0; i + 1 < d; i++) {
-      const uint64_t row = (uint64_t)(mR[b + i] - hub0) * h - hub0;
-      for (uint32_t j = i + 1 + lane; j < d; j += 32) atomicAdd(&CL[row + mR[b + j]], 1u);
+      const uint32_t a = mR[b + i] - hub0;
+      for (uint32_t j = i + 1 + lane; j < d; j += 32) atomicAdd(&CL[(uint64_t)(mR[b + j] - hub0) * h + a], 1u);
     }
   }
   if (lane == 0 && mine) atomicAdd(npairs, mine);
@@ -139,12 +139,12 @@ __global__ void k_light_pairs(const uint64_t *offM, const uint32_t *mR, const ui
 // tensor-core tiles: C_ij = A_i A_j^T over upper-triangle tile pairs (ti <= tj)
 // ---------------------------------------------------------------------------
 // strip t: tile row ti and its first tile column tj0 (row ti has
-// ceil((nt - ti) / SW) strips, tj0 = ti, ti + SW, ...)
-__device__ __forceinline__ void strip_of(uint32_t t, uint32_t nt, uint32_t &ti, uint32_t &tj0) {
+// ceil((nt - ti) / sw) strips, tj0 = ti, ti + sw, ...)
+__device__ __forceinline__ void strip_of(uint32_t t, uint32_t nt, uint32_t sw, uint32_t &ti, uint32_t &tj0) {
   uint32_t i = 0, rem = t;
-  while (rem >= (nt - i + SW - 1) / SW) { rem -= (nt - i + SW - 1) / SW; i++; }
+  while (rem >= (nt - i + sw - 1) / sw) { rem -= (nt - i + sw - 1) / sw; i++; }
   ti = i;
-  tj0 = i + rem * SW;
+  tj0 = i + rem * sw;
 }
 
 // Wait for phase `parity` of an mbarrier for at most limit_ns of global time;
@@ -187,7 +187,8 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
 // for its MMAs, and only then releases its tensor memory and exits.
 __global__ void __launch_bounds__(HB_THREADS) k_hub_mma(const __grid_constant__ CUtensorMap amap, uint32_t Kp,
                                                         uint32_t h, const unsigned int *CL, unsigned int *queue,
-                                                        unsigned long long *B, uint32_t *err, uint64_t wait_ns) {
+                                                        unsigned long long *B, uint32_t *err, uint64_t wait_ns,
+                                                        uint32_t sw) {
   extern __shared__ uint8_t hub_smem[];
   __shared__ __align__(8) uint64_t full[2], empty[2], done;
   __shared__ uint32_t tmem_holder, sh_item, sh_ok;
@@ -196,7 +197,7 @@ __global__ void __launch_bounds__(HB_THREADS) k_hub_mma(const __grid_constant__ 
   const uint32_t st0 = (smem_u32(hub_smem) + 1023u) & ~1023u;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
-                 "r"(SW * TM));
+                 "r"(sw * TM));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(HB_THREADS) k_hub_mma(const __grid_constant__ 
   const uint32_t taddr = tmem_holder;
   const uint32_t nt = h / TM, nchunks = Kp / KC;
   uint32_t nitems = 0;
-  for (uint32_t i = 0; i < nt; i++) nitems += (nt - i + SW - 1) / SW;
+  for (uint32_t i = 0; i < nt; i++) nitems += (nt - i + sw - 1) / sw;
   uint32_t q = 0;      // chunks issued so far by this CTA (thread 0): stage q & 1, its use q >> 1
   uint32_t q_iss = 0;  // chunk copies issued (thread 0)
   uint32_t q_ful = 0;  // chunk copies waited for (thread 0): those in [q_ful, q_iss) may be in flight
@@ -234,8 +235,8 @@ __global__ void __launch_bounds__(HB_THREADS) k_hub_mma(const __grid_constant__ 
     const uint32_t it = sh_item;
     if (it >= nitems) break;
     uint32_t ti, tj0;
-    strip_of(it, nt, ti, tj0);
-    const uint32_t w = min((uint32_t)SW, nt - tj0);  // tiles in this strip
+    strip_of(it, nt, sw, ti, tj0);
+    const uint32_t w = min(sw, nt - tj0);  // tiles in this strip
     if (tid == 0) {
       bool ok = true;
       if (q >= 2) ok = mbar_wait_bounded(smem_u32(&empty[q & 1]), ((q - 2) >> 1) & 1, wait_ns);
@@ -315,7 +316,8 @@ __global__ void __launch_bounds__(HB_THREADS) k_hub_mma(const __grid_constant__ 
         for (int k = 0; k < 8; k++) {
           const uint32_t gj = tj * TM + c0 + k;
           if (gj <= gi) continue;
-          const uint64_t c = (uint64_t)__uint_as_float(r[k]) + CL[(uint64_t)gi * h + gj];
+          // C_L is stored with the higher hub as the row: lanes (gi) read adjacent words
+          const uint64_t c = (uint64_t)__uint_as_float(r[k]) + CL[(uint64_t)gj * h + gi];
           if (c > 1) acc += c * (c - 1) / 2;
         }
       }
@@ -327,7 +329,7 @@ __global__ void __launch_bounds__(HB_THREADS) k_hub_mma(const __grid_constant__ 
   if (lane == 0 && acc) atomicAdd(B, acc);
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(SW * TM));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(sw * TM));
 }
 
 __global__ void k_min_rank(const uint32_t *list, uint32_t n, unsigned int *out) {
@@ -485,15 +487,25 @@ int hub_block_count(bfc_graph *g, Plan &p, uint32_t h, uint32_t tau, unsigned lo
     count_launch();
     profile_end("hub.light", s);
   }
+  // strips of four tiles, or of two (or one) when four would leave more than
+  // half of the SMs idle (narrower strips reload the shared A_i chunk more
+  // often: at 3,840 hubs, 240 two-tile strips measured 0.65 ms against 0.39
+  // for 128 four-tile strips)
+  const uint64_t sms = (uint64_t)sm_count_hub() * HB_PER_SM;
+  uint32_t sw = SW;
   uint64_t nitems = 0;
-  for (uint32_t i = 0; i < h / TM; i++) nitems += (h / TM - i + SW - 1) / SW;
-  const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)sm_count_hub() * HB_PER_SM, nitems);
+  for (;; sw >>= 1) {
+    nitems = 0;
+    for (uint32_t i = 0; i < h / TM; i++) nitems += (h / TM - i + sw - 1) / sw;
+    if (2 * nitems >= sms || sw == 1) break;
+  }
+  const unsigned grid = (unsigned)std::min<uint64_t>(sms, nitems);
   CUtensorMap amap;
   HB_TRY(hub_tensor_map(&amap, A.p, h, Kp));
   HB_CUDA(cudaFuncSetAttribute(k_hub_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HB_SMEM));
   profile_begin("hub.total", s);
   k_hub_mma<<<grid, HB_THREADS, HB_SMEM, s>>>(amap, Kp, h, ptr<unsigned int>(CL), queue, d_B, ptr<uint32_t>(g->err),
-                                              g_wait_ns ? g_wait_ns : WAIT_NS);
+                                              g_wait_ns ? g_wait_ns : WAIT_NS, sw);
   count_launch();
   profile_end("hub.total", s);
   HB_CUDA(cudaGetLastError());
