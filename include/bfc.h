@@ -377,7 +377,7 @@ int bfc_profile_read(const char *tag, uint64_t *launches, double *total_ms);
  *   small_max_segs  : the others whose wedge lists hold at most this many
  *                     segments of 512 wedges (plus one per row), or who have
  *                     at most half this many rows (their segments are then
- *                     lengthened), run in the 128-thread window CTAs (twelve
+ *                     lengthened), run in the 128-thread window CTAs (eleven
  *                     per SM, 16 KB counter windows); the rest, up to 1,280
  *                     segments or 640 rows, in the 512-thread CTAs (three per
  *                     SM, 48 KB windows), and beyond that in the big-class

@@ -12,7 +12,7 @@
 //   skip   degree < 2 or nothing after it: every c <= 1, contributes 0
 //   warp   <= 512 wedges: one warp per vertex, open addressing in shared memory
 //   small windows (<= 128 wedge-list segments of 512 targets, or at most 64
-//          rows with longer segments): a 128-thread CTA (twelve per SM) with
+//          rows with longer segments): a 128-thread CTA (eleven per SM) with
 //          4,096 counter words in shared memory
 //   large windows (<= 1,280 segments, or at most 640 rows): a 512-thread CTA
 //          (three per SM) with 12,288 words
@@ -73,7 +73,7 @@ constexpr uint64_t WH_MAX_WORK = WH_SLOTS / 2;    // load factor <= 1/2
 // start vertex at a time through a chain of dependent phases (row loads,
 // segment table, each window's count, read and clear, each closed by a CTA
 // barrier), so many small CTAs per SM hide that chain better than a few large
-// ones.  Small: twelve 128-thread CTAs per SM, each with 4,096 counter words
+// ones.  Small: eleven 128-thread CTAs per SM, each with 4,096 counter words
 // and room for 128 wedge-list segments; measured faster than six 256-thread
 // CTAs with 8,192 words, three 512-thread ones with 16,384 words, four
 // 384-thread ones or eight 192-thread ones.  A vertex of at most half as many
@@ -85,9 +85,9 @@ constexpr uint64_t WH_MAX_WORK = WH_SLOTS / 2;    // load factor <= 1/2
 template <int P>
 struct WinCfg;
 template <>
-struct WinCfg<4> {  // small: 12 CTAs of 4 warps per SM, 16 KB windows
+struct WinCfg<4> {  // small: 11 CTAs of 4 warps per SM, 16 KB windows
   static constexpr int THREADS = 128;
-  static constexpr int MINB = 12;
+  static constexpr int MINB = 11;  // 11 x (18.9 KB + 1 KB reserved) fit the SM's 228 KB, 12 do not
   static constexpr uint32_t WORDS = 4 * 1024;
   static constexpr uint32_t SMAX = 128;
   static constexpr size_t SMEM = (size_t)WORDS * 4 + (size_t)SMAX * 5 * 4;
@@ -767,7 +767,7 @@ __device__ __forceinline__ bool count_hl(const WArgs &a, uint64_t rb, uint64_t r
 }
 
 // (the whole-row modes, off the default path, are compiled for two fewer resident
-// CTAs: their read sweep needs a few more registers than the 42 that twelve
+// CTAs: their read sweep needs a few more registers than the 46 that eleven
 // 128-thread CTAs leave)
 template <int MODE, int CW, int P>
 __global__ void __launch_bounds__(WinCfg<P>::THREADS, (Full<MODE>::value && WinCfg<P>::MINB > 4) ? WinCfg<P>::MINB - 2 : WinCfg<P>::MINB) k_cta_win(WArgs a) {

@@ -45,12 +45,12 @@ def test_window_and_warp_kernels_do_not_spill(tmp_path):
     assert len(hot) >= 40, sorted(rep)
     for k, (regs, st, ld) in hot.items():
         assert st == 0 and ld == 0, (k, regs, st, ld)
-    # twelve 128-thread CTAs per SM for the ordered sweeps (modes 0, 1): at most
-    # 42 registers a thread; ten for the whole-row ones (at most 51)
+    # eleven 128-thread CTAs per SM for the ordered sweeps (modes 0, 1): at most
+    # 46 registers a thread; nine for the whole-row ones (at most 56)
     small = [v[0] for k, v in hot.items() if re.search(r"k_cta_winILi[01]ELi\d+ELi4E", k)]
-    assert small and max(small) <= 42
+    assert small and max(small) <= 46
     full = [v[0] for k, v in hot.items() if re.search(r"k_cta_winILi[23]ELi\d+ELi4E", k)]
-    assert full and max(full) <= 51
+    assert full and max(full) <= 56
 
 
 @pytest.mark.skipif(not os.path.exists(NVCC), reason="needs nvcc")
