@@ -105,3 +105,32 @@ def test_samplers_draws_match_oracle(big):
     oe, ocd, obd = O.wsamp_trial(g.u, g.v, g.nU, g.nV, 300, 98, 0)
     assert np.array_equal(u64(cd), ocd) and np.array_equal(u64(bd), obd)
     assert est[0] == pytest.approx(oe, rel=1e-12)
+
+
+def test_vertices_and_edges_of_every_degree_band(big):
+    """b_v and b_e of vertices drawn at random from every start-side degree band
+    (the kernels' classes split on degree: counter widths at 3, 15 and 255; the
+    window classes at 64 and 640 rows; the highest ranks take the hub block or
+    the flat expansion), against the oracle computed one by one."""
+    g, G = big
+    bU, bV, B = G.per_vertex()
+    bU = u64(bU)
+    be, _ = G.per_edge()
+    be = u64(be)
+    dU = np.bincount(g.u, minlength=g.nU)
+    rng = np.random.default_rng(77)
+    ids = []
+    for lo, hi in ((2, 3), (4, 15), (16, 64), (65, 255), (256, 640), (641, 1 << 30)):
+        pool = np.nonzero((dU >= lo) & (dU <= hi))[0]
+        if pool.size:
+            ids.append(rng.choice(pool, min(25, pool.size), replace=False))
+    ids = np.unique(np.concatenate(ids)).astype(np.uint32)
+    assert np.array_equal(bU[ids], O.per_vertex_list(g.u, g.v, g.nU, g.nV, 0, ids))
+    # the first and the last edge of each sampled vertex's row (canonical ids)
+    offU = np.zeros(g.nU + 1, np.int64)
+    np.cumsum(dU, out=offU[1:])
+    eidx = np.unique(np.concatenate([offU[ids], offU[ids + 1] - 1])).astype(np.uint64)
+    cu, cv = G.edges()
+    cu = cu.cpu().numpy().astype(np.uint32)
+    cv = cv.cpu().numpy().astype(np.uint32)
+    assert np.array_equal(be[eidx.astype(np.int64)], O.per_edge_list(cu, cv, g.nU, g.nV, eidx))
