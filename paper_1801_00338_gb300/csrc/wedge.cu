@@ -37,7 +37,8 @@
 // modes a vertex first tries the heavy-light split (count_hl): its lists other
 // than the longest in a small hash table, the longest streamed once against
 // it; in EDGE mode a vertex whose other lists are too long for the table walks
-// the windows with the longest list as their heavy list (heavy_piece).
+// the windows with the longest list as their heavy list, walked by the whole
+// CTA after each window's count (heavy_walk).
 //
 // Modes: TOTAL (B only), EDGE (b_e; the vertex counts follow from b_e),
 // SINGLE (Algorithm 2 on a batch of vertices: every w != v, whole midpoint
@@ -323,6 +324,28 @@ __global__ void __launch_bounds__(WH_WARPS * 32) k_warp_class(WArgs a) {
 
 // ---------------------------------------------------------------------------
 // window classes: packed dense counters in shared memory
+// Predicated atomics: the sweeps' per-target updates are issued under a
+// predicate instead of inside a branch, so a warp whose lanes disagree does
+// not diverge around them.
+// shared-memory add returning the old word; 0 (and no add) where p is false
+__device__ __forceinline__ uint32_t atom_add_if(bool p, uint32_t *addr, uint32_t v) {
+  uint32_t old = 0;
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(addr);
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %1, 0;\n\t@q atom.shared.add.u32 %0, [%2], %3;\n\t}"
+      : "+r"(old)
+      : "r"((uint32_t)p), "r"(sa), "r"(v)
+      : "memory");
+  return old;
+}
+// global 64-bit add where p is true (no return value)
+__device__ __forceinline__ void red_add_if(bool p, unsigned long long *addr, unsigned long long v) {
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q red.global.add.u64 [%1], %2;\n\t}"
+               :
+               : "r"((uint32_t)p), "l"(addr), "l"(v)
+               : "memory");
+}
+
 // ---------------------------------------------------------------------------
 // Counter of window offset idx: word idx mod WIN_WORDS, field idx / WIN_WORDS,
 // so consecutive ranks (a sorted wedge list) fall in consecutive words and
@@ -344,6 +367,12 @@ struct Ctr {
     at(idx, wi, sh);
     return (atomicAdd(&c[wi], 1u << sh) >> sh) & MASK;
   }
+  // the same under a predicate, with no branch around it: 0 where p is false
+  __device__ static __forceinline__ uint32_t inc_get_if(bool p, uint32_t *c, uint32_t idx) {
+    uint32_t wi, sh;
+    at(idx, wi, sh);
+    return (atom_add_if(p, &c[wi], 1u << sh) >> sh) & MASK;
+  }
   __device__ static __forceinline__ uint32_t peek(const uint32_t *c, uint32_t idx) {
     uint32_t wi, sh;
     at(idx, wi, sh);
@@ -363,6 +392,21 @@ __device__ __forceinline__ void count_segment(const uint32_t *__restrict__ mR, u
                                               uint32_t lo, uint32_t hi, uint32_t r, uint32_t *ctr, uint32_t &nx,
                                               uint64_t &acc) {
   const int lane = threadIdx.x & 31;
+  using C = Ctr<CW, WIN_WORDS>;
+  {
+    // the first 32 alone: most pieces end within them
+    const uint32_t i = cur + lane;
+    const uint32_t w = (i < end) ? __ldg(&mR[i]) : INF_RANK;
+    const bool in = w < hi;
+    const uint32_t n = __popc(__ballot_sync(0xffffffffu, in));
+    acc += C::inc_get_if(in && (!Full<MODE>::value || w != r), ctr, w - lo);
+    cur += n;
+    if (n < 32) {
+      const uint32_t first_out = __shfl_sync(0xffffffffu, w, n & 31);
+      nx = (cur < end) ? first_out : INF_RANK;
+      return;
+    }
+  }
   while (true) {
     uint32_t w[4];
 #pragma unroll
@@ -374,7 +418,7 @@ __device__ __forceinline__ void count_segment(const uint32_t *__restrict__ mR, u
     for (int k = 0; k < 4; k++) {
       const bool in = w[k] < hi;
       const uint32_t bal = __ballot_sync(0xffffffffu, in);
-      if (in && (!Full<MODE>::value || w[k] != r)) acc += Ctr<CW, WIN_WORDS>::inc_get(ctr, w[k] - lo);
+      acc += C::inc_get_if(in && (!Full<MODE>::value || w[k] != r), ctr, w[k] - lo);
       const uint32_t n = __popc(bal);
       cur += n;
       if (n < 32) {
@@ -387,27 +431,30 @@ __device__ __forceinline__ void count_segment(const uint32_t *__restrict__ mR, u
 }
 
 // The heavy list in a window (the split of count_hl with windows): the
-// vertex's longest wedge list is not counted; after the window's light counts
-// are final, the warp walks one of its segments from cur.  Targets below lo
-// lie where no light list has a target (c_L = 0) and are passed over; a
-// target w in [lo, hi) adds c_L(w) = peek(w - lo) to acc, and in EDGE mode
+// vertex's longest wedge list is not counted and not segmented; after the
+// window's light counts are final, every warp of the CTA walks it from cur
+// (mR[cur, end)), warp k taking the 128-entry chunks k, k + NW, ... .
+// Targets below lo lie where no light list has a target (c_L = 0) and are
+// passed over; a target w in [lo, hi) adds c_L(w) = peek(w - lo) to rs (this
+// lane's near-edge sum, which is also the vertex's B share), and in EDGE mode
 // raises its counter by one (so the read sweep sees c = c_L + 1) and adds c_L
-// to the far edge (staged at beM[i]) and to the returned near-edge sum (valid
-// in lane 0).  On return cur is the first target >= hi (or end), nx its rank
-// (INF_RANK at the end), hit whether some c_L was > 0.
-template <int MODE, int CW, uint32_t WIN_WORDS>
-__device__ __forceinline__ uint64_t heavy_piece(const uint32_t *__restrict__ mR, unsigned long long *beM,
-                                                uint32_t &cur, uint32_t end, uint32_t lo, uint32_t hi, uint32_t *ctr,
-                                                uint32_t &nx, uint64_t &acc, bool &hit) {
+// to the far edge (staged at beM[i]); hit records some c_L > 0.  Targets are
+// ascending, so each warp stops at its first chunk with a target >= hi (or at
+// end) and reports that position to *pos_min: their minimum is the list's
+// first target >= hi, its cursor for the next window.
+template <int MODE, int CW, uint32_t WIN_WORDS, int NW>
+__device__ __forceinline__ void heavy_walk(const uint32_t *__restrict__ mR, unsigned long long *beM, uint32_t cur,
+                                           uint32_t end, uint32_t lo, uint32_t hi, uint32_t *ctr, uint32_t *pos_min,
+                                           uint64_t &rs, bool &hit) {
   using C = Ctr<CW, WIN_WORDS>;
-  const int lane = threadIdx.x & 31;
-  uint64_t rs = 0;
-  while (true) {
-    const uint32_t base = cur;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr uint32_t STRIDE = NW * 128u;
+  uint32_t c0 = cur + (uint32_t)warp * 128u;
+  while (c0 < end) {
     uint32_t w[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-      const uint32_t i = base + k * 32 + lane;
+      const uint32_t i = c0 + k * 32 + lane;
       w[k] = (i < end) ? __ldg(&mR[i]) : INF_RANK;
     }
 #pragma unroll
@@ -417,24 +464,24 @@ __device__ __forceinline__ uint64_t heavy_piece(const uint32_t *__restrict__ mR,
       if (in && w[k] >= lo) {
         const uint32_t c = C::peek(ctr, w[k] - lo);
         if (c) {
-          acc += c;
+          rs += c;
           hit = true;
           if (MODE == MODE_EDGE) {
             C::inc_get(ctr, w[k] - lo);
-            rs += c;
-            atomicAdd(&beM[base + k * 32 + lane], (unsigned long long)c);
+            atomicAdd(&beM[c0 + k * 32 + lane], (unsigned long long)c);
           }
         }
       }
       const uint32_t n = __popc(bal);
-      cur += n;
       if (n < 32) {
-        const uint32_t first_out = __shfl_sync(0xffffffffu, w[k], n & 31);
-        nx = (cur < end) ? first_out : INF_RANK;
-        return warp_sum_u64_small(rs);
+        if (lane == 0) atomicMin(pos_min, c0 + k * 32 + n);
+        return;
       }
     }
+    if (end - c0 <= STRIDE) break;
+    c0 += STRIDE;
   }
+  if (lane == 0) atomicMin(pos_min, end);
 }
 
 // Read sweep of one counted piece mR[ps, pe) of a wedge list (EDGE and
@@ -448,7 +495,8 @@ __device__ __forceinline__ uint64_t read_piece(const uint32_t *__restrict__ mR, 
                                                uint32_t pe, uint32_t lo, Peek peek) {
   const int lane = threadIdx.x & 31;
   uint64_t rowsum = 0;
-  for (uint32_t i0 = ps; i0 < pe; i0 += 128) {
+  uint32_t i0 = ps;
+  for (; i0 + 32 < pe; i0 += 128) {
     uint32_t w[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) {
@@ -458,14 +506,20 @@ __device__ __forceinline__ uint64_t read_piece(const uint32_t *__restrict__ mR, 
 #pragma unroll
     for (int k = 0; k < 4; k++) {
       const uint32_t i = i0 + k * 32 + lane;
-      if (i < pe) {
-        const uint32_t c = peek(w[k] - lo);
-        if (c > 1) {
-          rowsum += c - 1;
-          if (MODE != MODE_LOCAL) atomicAdd(&beM[i], (unsigned long long)(c - 1));
-        }
-      }
+      const uint32_t c = (i < pe) ? peek(w[k] - lo) : 0u;
+      const bool p = c > 1;
+      rowsum += p ? c - 1 : 0u;
+      if (MODE != MODE_LOCAL) red_add_if(p, &beM[i], (unsigned long long)(c - 1));
     }
+  }
+  if (i0 < pe) {
+    // the last (often the only) 32 targets
+    const uint32_t i = i0 + lane;
+    const uint32_t w = (i < pe) ? __ldg(&mR[i]) : 0u;
+    const uint32_t c = (i < pe) ? peek(w - lo) : 0u;
+    const bool p = c > 1;
+    rowsum += p ? c - 1 : 0u;
+    if (MODE != MODE_LOCAL) red_add_if(p, &beM[i], (unsigned long long)(c - 1));
   }
   return warp_sum_u64_small(rowsum);
 }
@@ -786,7 +840,9 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, (Full<MODE>::value && WinC
   __shared__ uint32_t sh_idx, sh_carry;
   __shared__ unsigned long long sh_acc, sh_hmax;
   __shared__ uint32_t sh_hj;  // the vertex's heavy list (row index), INF_RANK: none
-  __shared__ uint32_t sh_heid;  // its start-row edge id (the segments' s_row), INF_RANK: none
+  __shared__ uint32_t sh_heid;  // its start-row edge id, INF_RANK: none
+  __shared__ uint32_t sh_hb, sh_he;  // its wedge list mR[sh_hb, sh_he) (not segmented)
+  __shared__ uint32_t sh_hpos[2];  // per window parity: where its walk stopped
   __shared__ uint32_t sh_seglen;  // segment length of the vertex (ordered modes)
   __shared__ uint32_t wtot[32];
   constexpr int NW = WIN_THREADS / 32;
@@ -809,6 +865,8 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, (Full<MODE>::value && WinC
       sh_hmax = 0;
       sh_hj = INF_RANK;
       sh_heid = INF_RANK;
+      sh_hb = sh_he = 0;
+      sh_hpos[0] = sh_hpos[1] = INF_RANK;
       sh_min[0] = INF_RANK; sh_win[0] = 0;
       sh_min[1] = INF_RANK; sh_win[1] = 0;
     }
@@ -858,7 +916,13 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, (Full<MODE>::value && WinC
         e = (uint32_t)a.offM[x + 1];
         ns = (e - b + seglen - 1) / seglen;
         eid = a.sEid[j];
-        if ((uint32_t)(j - rb) == sh_hj) sh_heid = eid;
+        if ((uint32_t)(j - rb) == sh_hj) {
+          // the heavy list is walked by the whole CTA after each window's count
+          sh_heid = eid;
+          sh_hb = b;
+          sh_he = e;
+          ns = 0;
+        }
       }
       const uint32_t incl = warp_incl_scan_u32(ns);
       if (lane == 31) wtot[warp] = incl;
@@ -883,6 +947,8 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, (Full<MODE>::value && WinC
       __syncthreads();
     }
     const uint32_t nseg = min(sh_carry, WIN_SMAX);
+    uint32_t hcur = sh_hb;  // the heavy list's cursor (the same in every thread)
+    const uint32_t hend = sh_he;
     uint32_t lo = lo0;
     uint32_t hi = (uint32_t)umin64((uint64_t)a.nS, (uint64_t)lo + Z);
     for (uint32_t par = 0;; par ^= 1) {
@@ -896,7 +962,7 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, (Full<MODE>::value && WinC
         bool act = false;
         if (sl < nseg) {
           const uint32_t c0 = s_cur[sl];
-          my_nx = (c0 < s_end[sl] && s_row[sl] != sh_heid) ? s_nx[sl] : INF_RANK;
+          my_nx = (c0 < s_end[sl]) ? s_nx[sl] : INF_RANK;
           act = my_nx < hi;  // 0: next target not loaded yet
           s_ps[sl] = c0;     // nothing of it counted in this window yet
         }
@@ -935,27 +1001,18 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, (Full<MODE>::value && WinC
       const uint32_t nm = sh_min[par];
       // ---- the heavy list against the window's final light counts
       if (sh_hj != INF_RANK) {
+        if (threadIdx.x == 0) sh_hpos[par ^ 1] = INF_RANK;
         bool hit = false;
-        for (uint32_t s0 = warp; s0 < nseg; s0 += NW * 32) {
-          const uint32_t sl = s0 + (uint32_t)lane * NW;
-          const bool act = sl < nseg && s_row[sl] == sh_heid && s_cur[sl] < s_end[sl] && s_nx[sl] < hi;
-          uint32_t bal = __ballot_sync(0xffffffffu, act);
-          while (bal) {
-            const int l = __ffs(bal) - 1;
-            bal &= bal - 1;
-            const uint32_t sg = s0 + (uint32_t)l * NW;
-            uint32_t cur = s_cur[sg], nx = INF_RANK;
-            const uint64_t rs = heavy_piece<MODE, CW, WIN_WORDS>(a.mR, a.beM, cur, s_end[sg], lo, hi, ctr, nx, acc,
-                                                                 hit);
-            if (lane == 0) {
-              s_cur[sg] = cur;
-              s_nx[sg] = nx;
-              if (MODE == MODE_EDGE && rs) atomicAdd(&a.be[sh_heid], (unsigned long long)rs);
-            }
-          }
+        uint64_t rs = 0;
+        heavy_walk<MODE, CW, WIN_WORDS, NW>(a.mR, a.beM, hcur, hend, lo, hi, ctr, &sh_hpos[par], rs, hit);
+        acc += rs;
+        if (MODE == MODE_EDGE) {
+          const uint64_t t = warp_sum_u64_small(rs);
+          if (lane == 0 && t) atomicAdd(&a.be[sh_heid], (unsigned long long)t);
+          if (__any_sync(0xffffffffu, hit) && lane == 0) atomicAdd(&sh_win[par], 1ull);
         }
-        if (MODE == MODE_EDGE && __any_sync(0xffffffffu, hit) && lane == 0) atomicAdd(&sh_win[par], 1ull);
         __syncthreads();
+        hcur = sh_hpos[par];
       }
       // ---- EDGE / LOCAL: every wedge of the window reads its final count
       if (MODE == MODE_EDGE || MODE == MODE_LOCAL) {
@@ -963,7 +1020,7 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, (Full<MODE>::value && WinC
           // the same ownership: each warp reads back the pieces it counted
           for (uint32_t s0 = warp; s0 < nseg; s0 += NW * 32) {
             const uint32_t sl = s0 + (uint32_t)lane * NW;
-            const bool act = sl < nseg && s_ps[sl] < s_cur[sl] && s_row[sl] != sh_heid;
+            const bool act = sl < nseg && s_ps[sl] < s_cur[sl];
             uint32_t bal = __ballot_sync(0xffffffffu, act);
             while (bal) {
               const int l = __ffs(bal) - 1;

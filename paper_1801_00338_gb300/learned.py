@@ -195,18 +195,6 @@ def draws_for_median_error(var1: float, B: float, rel: float = 0.01) -> int:
     return max(1, int(math.ceil((0.6744897501960817 / rel) ** 2 * var1 / (B * B))))
 
 
-def time_vsamp(G: "bfc.Graph", k: int, trials: int, seed: int, prop=None, reps: int = 3) -> float:
-    """Mean GPU wall time (s) of one bfc_vsamp call of `trials` x `k` draws."""
-    import torch
-    G.vsamp(k, trials, seed, proposal=prop)  # warm up (layouts of both sides)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for r in range(reps):
-        G.vsamp(k, trials, seed + 1 + r, proposal=prop)
-    torch.cuda.synchronize()
-    return (time.perf_counter() - t0) / reps
-
-
 def _train_graph_job(args):
     i, (nU, nV, m, gu, gv), seed = args
     u, v = synth.chung_lu_bipartite(nU, nV, m, gu, gv, seed)
@@ -302,90 +290,3 @@ def equal_time(G: "bfc.Graph", b: np.ndarray, B: int, wb, trials: int = 3, seed:
                         "s_for_target": k_u_pred * t_draw_u},
             "time_ratio_to_target": t_l / (k_u_pred * t_draw_u),
             "error_ratio_at_equal_time": float(np.median(err_l) / max(np.median(err_u), 1e-300))}
-
-
-def evaluate(train_count: int = 200, m_lo: float = 1e4, m_hi: float = 1e6, steps: int = 2000,
-             heldout=(5_000_000, 10_000_000, 100_000_000, 2.3, 2.3, 10_000), k_timing: int = 4096,
-             trials_check: int = 30, seed: int = 0, check_budget_s: float = 60.0) -> dict:
-    """Train on generated graphs, then compare uniform and learned VSamp on a
-    held-out graph: exact single-draw variances (from exact vBFC counts), the
-    draws each needs for a 1% median relative error, the GPU time per draw,
-    the time to 1% (the learned one includes features + network + proposal
-    build), and the median relative error of `trials_check` trials at those
-    draw counts."""
-    import torch
-    out = {"train_graphs": train_count, "train_m_range": [m_lo, m_hi], "steps": steps}
-    t0 = time.perf_counter()
-    params = training_graph_params(train_count, seed + 21, m_lo, m_hi)
-    graphs = []
-    for i, (nU, nV, m, gu, gv) in enumerate(params):
-        u, v = synth.chung_lu_bipartite(nU, nV, m, gu, gv, 10_000 + seed * 1000 + i)
-        graphs.append((u, v, nU, nV))
-    out["train_edges"] = int(sum(len(g[0]) for g in graphs))
-    out["gen_s"] = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    data = dataset_from_graphs(graphs)
-    del graphs
-    torch.cuda.synchronize()
-    out["label_s"] = time.perf_counter() - t0
-    tr = Trainer(seed=seed, lr=3e-3, out_bias=float(data.T.mean().item()))
-    out["mse_before"] = tr.mse(data)
-    t0 = time.perf_counter()
-    tr.fit(data, steps=steps, batch=65536)
-    torch.cuda.synchronize()
-    out["train_s"] = time.perf_counter() - t0
-    out["mse_after"] = tr.mse(data)
-    del data
-    nU, nV, m, gu, gv, hseed = heldout
-    h = synth.chung_lu_scaled(nU, nV, m, gu, gv, hseed)
-    out["heldout"] = {"nU": nU, "nV": nV, "m": m, "gamma": [gu, gv], "seed": hseed}
-    with bfc.Graph(h.u, h.v, h.nU, h.nV) as G:
-        bU, bV, B = G.per_vertex()
-        b = np.concatenate([bU.cpu().numpy(), bV.cpu().numpy()]).astype(np.float64)
-        out["heldout"]["B"] = int(B)
-        # proposal build time (features + forward + weights + prefix sums)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        prop = proposal(G, tr.wb)
-        torch.cuda.synchronize()
-        t_prop = time.perf_counter() - t0
-        q = mixture_q(prop, G.nU + G.nV)
-        var_u = single_draw_variance(b)
-        var_l = single_draw_variance(b, q)
-        k_u = draws_for_median_error(var_u, B)
-        k_l = draws_for_median_error(var_l, B)
-        t_u = time_vsamp(G, k_timing, 8, 7) / (8 * k_timing)
-        t_l = time_vsamp(G, k_timing, 8, 7, prop) / (8 * k_timing)
-        res = {"var_uniform": var_u, "var_learned": var_l, "var_ratio": var_l / var_u,
-               "draws_1pct_uniform": k_u, "draws_1pct_learned": k_l,
-               "s_per_draw_uniform": t_u, "s_per_draw_learned": t_l, "proposal_build_s": t_prop,
-               "time_1pct_uniform_s": k_u * t_u, "time_1pct_learned_s": k_l * t_l + t_prop}
-        res["time_ratio"] = res["time_1pct_learned_s"] / res["time_1pct_uniform_s"]
-        # empirical check at those draw counts (capped so that each check takes
-        # about `check_budget_s`); these long calls also give the per-draw
-        # times used for the time to 1%
-        for name, kk, p, t_pilot in (("uniform", k_u, None, t_u), ("learned", k_l, prop, t_l)):
-            kk = int(max(1, min(kk, check_budget_s / (trials_check * t_pilot))))
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            est = G.vsamp(kk, trials_check, 1234, proposal=p)
-            torch.cuda.synchronize()
-            res[f"s_per_draw_{name}_long"] = (time.perf_counter() - t0) / (kk * trials_check)
-            rel = np.abs(np.asarray(est) - B) / B
-            res[f"median_rel_err_{name}"] = float(np.median(rel))
-            res[f"draws_used_{name}"] = kk
-        res["time_1pct_uniform_s"] = k_u * res["s_per_draw_uniform_long"]
-        res["time_1pct_learned_s"] = k_l * res["s_per_draw_learned_long"] + t_prop
-        res["time_ratio"] = res["time_1pct_learned_s"] / res["time_1pct_uniform_s"]
-        bfc.bfc_proposal_free(prop)
-    out["vsamp"] = res
-    return out
-
-
-if __name__ == "__main__":
-    import json
-    import sys
-    kw = {}
-    if "--small" in sys.argv:
-        kw = dict(train_count=20, m_lo=5e3, m_hi=1e5, steps=400, heldout=(20_000, 40_000, 400_000, 2.3, 2.3, 10_000))
-    print(json.dumps(evaluate(**kw)))
