@@ -163,7 +163,7 @@ def bfc_launch_count() -> int:
     return int(load().bfc_launch_count())
 
 
-CLASSES = ("skip", "warp", "s2", "s4", "s8", "s16", "s32", "l2", "l4", "l8", "l16", "l32", "big")
+CLASSES = ("skip", "warp", "s2", "s4", "s8", "s6", "s5", "l2", "l4", "l8", "l16", "l10", "big")
 
 
 def bfc_plan_stats(h: int, side: int, stream=None) -> dict:
@@ -193,11 +193,11 @@ def bfc_profile_read(tag: str) -> tuple[int, float]:
 
 PROFILE_TAGS = [f"{c}.{m}" for c in ("warp", "win", "big") for m in ("total", "edge", "single", "local")]
 PROFILE_TAGS += ["hub.total", "hub.degree", "hub.light", "esamp.exact", "esamp.fast", "wsamp"]
-# the window kernels also per class: "win.edge.s8" (8-bit counters, 512-thread CTAs)
+# the window kernels also per class: "win.edge.s8" (8-bit counters, the 128-thread CTAs)
 WIN_CLASS_TAGS = [f"win.{m}.{c}" for m in ("total", "edge", "single", "local")
-                  for c in ("s2", "s4", "s8", "s16", "s32", "l2", "l4", "l8", "l16", "l32")]
+                  for c in ("s2", "s4", "s8", "s6", "s5", "l2", "l4", "l8", "l16", "l10")]
 # kernel tag -> the classes it runs
-TAG_CLASSES = {"warp": ("warp",), "win": ("s2", "s4", "s8", "s16", "s32", "l2", "l4", "l8", "l16", "l32"),
+TAG_CLASSES = {"warp": ("warp",), "win": ("s2", "s4", "s8", "s6", "s5", "l2", "l4", "l8", "l16", "l10"),
                "big": ("big",)}
 
 

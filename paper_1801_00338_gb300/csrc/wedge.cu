@@ -18,11 +18,14 @@
 //          (three per SM) with 12,288 words
 //   big    more: the large CTA with its segment cursors in global memory and a
 //          32-bit window
-// The window classes pack their counters by degree: 2 bits for degree <= 3,
-// 4 for <= 15, 8 for <= 255, 16 for <= 65,535, else 32, so a 4,096-word
-// window spans 65,536 ranks at 2 bits and 4,096 at 32.  Ranks ascend with
-// degree, so the low-rank vertices, which walk the most of the rank space,
-// are exactly the ones with the narrowest counters and the widest windows.
+// The window classes pack their counters by degree, 32 / b fields of b bits
+// to a word: small windows 2 bits for degree <= 3, 3 for <= 7, 4 for <= 15,
+// 5 for <= 31, else 8 (a small-class vertex has at most 127 rows); large
+// windows 2, 4, 5 and 8 bits likewise up to degree 255, else 16 (at most
+// 1,279 rows).  A 4,096-word window spans 65,536 ranks at 2 bits, 24,576 at
+// 5 and 16,384 at 8.  Ranks ascend with degree, so the low-rank vertices,
+// which walk the most of the rank space, are exactly the ones with the
+// narrowest counters and the widest windows.
 // The thresholds are scheduling settings (bfc_tuning); the counts do not
 // depend on them.
 //
@@ -64,7 +67,9 @@ constexpr uint32_t INF_RANK = 0xFFFFFFFFu;
 // large windows for the same widths, then big
 enum Cls : uint32_t { CLS_SKIP = 0, CLS_WARP = 1, CLS_S0 = 2, CLS_L0 = 7, CLS_BIG = 12 };
 static_assert(CLS_BIG + 1 == Plan::NCLS, "class count");
-constexpr int CW_OF[5] = {2, 4, 8, 16, 32};
+// counter bits of each window class slot, small and large (class_of)
+constexpr int CW_SMALL[5] = {2, 4, 8, 6, 5};
+constexpr int CW_LARGE[5] = {2, 4, 8, 16, 10};
 
 // warp class
 constexpr int WH_WARPS = 8;
@@ -1241,12 +1246,14 @@ __device__ __forceinline__ uint32_t class_of(uint64_t d, uint64_t w, ClsLimits l
   if (segs <= lim.small_max || (lim.adaptive && 2 * d <= lim.small_max)) base = CLS_S0;
   else if (segs <= LMAX || (lim.adaptive && 2 * d <= LMAX)) base = CLS_L0;
   else return CLS_BIG;
-  // counter width: every c(v, w) <= degree of v
+  // counter width (CW_SMALL / CW_LARGE): every c(v, w) <= degree of v
   if (d <= 3) return base + 0;
   if (d <= 15) return base + 1;
+  if (base == CLS_S0) return d <= 31 ? base + 4 : d <= 63 ? base + 3 : base + 2;  // (d <= 127 here)
   if (d <= 255) return base + 2;
+  if (d <= 1023) return base + 4;
   if (d <= 65535) return base + 3;
-  return base + 4;
+  return CLS_BIG;  // (not reached: a large-class vertex has d <= 1,279)
 }
 
 // Class of every start rank, with per-class vertex counts, wedge and row
@@ -1427,23 +1434,23 @@ static int launch_lists(bfc_graph *g, WArgs a, const uint32_t *const *lists, con
     WArgs w = a;
     setup(w, c);
     const bool small = c < CLS_L0;
-    const int cw = CW_OF[(c - CLS_S0) % 5];
+    const int cw = small ? CW_SMALL[c - CLS_S0] : CW_LARGE[c - CLS_L0];
     void (*kern)(WArgs) = nullptr;
     if (small) {
       kern = cw == 2 ? k_cta_win<MODE, 2, P_SMALL> : cw == 4 ? k_cta_win<MODE, 4, P_SMALL>
-           : cw == 8 ? k_cta_win<MODE, 8, P_SMALL> : cw == 16 ? k_cta_win<MODE, 16, P_SMALL>
-                                                              : k_cta_win<MODE, 32, P_SMALL>;
+           : cw == 5 ? k_cta_win<MODE, 5, P_SMALL> : cw == 6 ? k_cta_win<MODE, 6, P_SMALL>
+                                                            : k_cta_win<MODE, 8, P_SMALL>;
     } else {
       kern = cw == 2 ? k_cta_win<MODE, 2, P_LARGE> : cw == 4 ? k_cta_win<MODE, 4, P_LARGE>
-           : cw == 8 ? k_cta_win<MODE, 8, P_LARGE> : cw == 16 ? k_cta_win<MODE, 16, P_LARGE>
-                                                              : k_cta_win<MODE, 32, P_LARGE>;
+           : cw == 8 ? k_cta_win<MODE, 8, P_LARGE> : cw == 10 ? k_cta_win<MODE, 10, P_LARGE>
+                                                             : k_cta_win<MODE, 16, P_LARGE>;
     }
     const int per_sm = small ? WinCfg<P_SMALL>::MINB : WinCfg<P_LARGE>::MINB;
     const int threads = small ? WinCfg<P_SMALL>::THREADS : WinCfg<P_LARGE>::THREADS;
     const size_t smem = small ? WinCfg<P_SMALL>::SMEM : WinCfg<P_LARGE>::SMEM;
     BFC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // per-class timing as well ("win.edge.s8": the 8-bit small-window class)
-    static const char *cls_names[10] = {"s2", "s4", "s8", "s16", "s32", "l2", "l4", "l8", "l16", "l32"};
+    static const char *cls_names[10] = {"s2", "s4", "s8", "s6", "s5", "l2", "l4", "l8", "l16", "l10"};
     const std::string ctag = std::string(tag_of(1, MODE)) + "." + cls_names[c - CLS_S0];
     profile_begin(ctag.c_str(), s);
     kern<<<cap((unsigned)(sms * per_sm), c), threads, smem, s>>>(w);
