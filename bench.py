@@ -42,8 +42,8 @@ CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.a
 # DRAM bytes (read + write) per call of each counting-kernel set, from one ncu
 # capture of the kernels' dram__bytes counters, valid only for the kernel
 # source they were taken with (its SHA-256 prefix).
-MEASURED_TRAFFIC = {"source_sha256": "30b01499a930ad50",
-                    "bytes": {"win.edge": 17.21e9, "win.total": 5.932e9}}
+MEASURED_TRAFFIC = {"source_sha256": "090c5151bfffdd73",
+                    "bytes": {"win.edge": 17.10e9, "win.total": 5.947e9}}
 
 
 def measured_traffic(tag: str):
@@ -368,7 +368,7 @@ def extra_vsamp(bfc) -> dict:
         del h
         bU, bV, B = G.per_vertex()
         b = np.concatenate([bU.cpu().numpy(), bV.cpu().numpy()]).astype(np.float64)
-        res = Ln.equal_time(G, b, int(B), tr.wb, trials=3, seed=7)
+        res = Ln.equal_time(G, b, int(B), tr.wb, trials=9, seed=7, rel=0.02)
     res["training"] = info
     res["heldout"] = {"workload": "chung_lu_U5M_V10M_E100M_g2.3_2.3_seed10000", "B": int(B)}
     return res

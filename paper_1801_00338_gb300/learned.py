@@ -282,11 +282,15 @@ def equal_time(G: "bfc.Graph", b: np.ndarray, B: int, wb, trials: int = 3, seed:
         bfc.bfc_proposal_free(prop)
     err_l = np.abs(np.asarray(est_l, np.float64) - B) / B
     err_u = np.abs(np.asarray(est_u, np.float64) - B) / B
+    # the median relative error the exact single-draw variance predicts (normal
+    # approximation: the median of |N(0, 1)| is 0.6745)
+    pred = lambda var1, k: 0.6744897501960817 * math.sqrt(var1 / k) / B
     return {"trials": trials, "target_rel_err": rel,
             "learned": {"draws": int(k_l), "s_per_trial": t_l, "proposal_build_s": t_prop,
-                        "median_rel_err": float(np.median(err_l)), "var_single_draw": var_l},
+                        "median_rel_err": float(np.median(err_l)), "predicted_median_rel_err": pred(var_l, k_l),
+                        "var_single_draw": var_l},
             "uniform": {"draws": int(k_u), "s_per_trial": t_u, "median_rel_err": float(np.median(err_u)),
-                        "var_single_draw": var_u, "draws_for_target": int(k_u_pred),
-                        "s_for_target": k_u_pred * t_draw_u},
+                        "predicted_median_rel_err": pred(var_u, k_u), "var_single_draw": var_u,
+                        "draws_for_target": int(k_u_pred), "s_for_target": k_u_pred * t_draw_u},
             "time_ratio_to_target": t_l / (k_u_pred * t_draw_u),
             "error_ratio_at_equal_time": float(np.median(err_l) / max(np.median(err_u), 1e-300))}
