@@ -402,8 +402,8 @@ int bfc_profile_read(const char *tag, uint64_t *launches, double *total_ms);
  *                     longest hold at most this many wedges is counted without
  *                     windows: those lists in a shared-memory hash table, the
  *                     longest one streamed once against it.  Default 0: as
- *                     many as the table holds at half load (512 in the 128-thread CTAs,
- *                     1,024 in the 512-thread ones);
+ *                     many as the table holds at three-quarter load (768 in
+ *                     the 128-thread CTAs, 1,536 in the 512-thread ones);
  *                     BFC_TUNE_NO_HL never.
  * A changed class limit redoes the cached classification of the start
  * vertices on the next counting call (the rank layout is kept).

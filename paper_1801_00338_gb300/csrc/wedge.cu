@@ -641,6 +641,12 @@ __device__ __forceinline__ void count_flat(const WArgs &a, uint32_t r, uint64_t 
 // The table holds at most half as many keys as slots, so every probe
 // sequence ends at an empty slot or the key.
 constexpr uint32_t HL_FLAG = 0x80000000u;
+// light wedges of the split at most: HL_FILL quarters of the largest table
+// (its bitmap still turns most heavy-list misses away at that load; the light
+// lookups walk somewhat longer probe sequences)
+#ifndef HL_FILL
+#define HL_FILL 3
+#endif
 #ifndef HL_U
 #define HL_U 4
 #endif
@@ -682,13 +688,14 @@ __device__ __forceinline__ uint32_t hl_row(const uint32_t *pre, uint32_t d, uint
 }
 
 // Count start vertex r (rows [rb, re), 1 <= re - rb <= THREADS) by the split
-// above if its light lists hold at most tmax / 2 wedges; returns false (after
-// a barrier, nothing written) otherwise.  ctr: the WORDS zeroed counter words (left
+// above if its light lists hold at most wmax wedges (below tmax, the power of
+// two of table slots that fits); returns false (after a barrier, nothing
+// written) otherwise.  ctr: the WORDS zeroed counter words (left
 // zeroed); area: 4 THREADS + 4 free words (8-byte aligned); sh_hmax: a shared
 // word the caller zeroed before the vertex.  All threads call it together.
 template <int MODE, int THREADS, uint32_t WORDS>
 __device__ __forceinline__ bool count_hl(const WArgs &a, uint64_t rb, uint64_t re, uint64_t work, uint32_t *ctr,
-                                         uint32_t tmax, uint32_t *area, unsigned long long *sh_hmax,
+                                         uint32_t tmax, uint32_t wmax, uint32_t *area, unsigned long long *sh_hmax,
                                          uint32_t *sh_wt, uint64_t &acc) {
   constexpr int NW = THREADS / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -711,9 +718,10 @@ __device__ __forceinline__ bool count_hl(const WArgs &a, uint64_t rb, uint64_t r
   const unsigned long long hk = *sh_hmax;
   const uint32_t hlen = (uint32_t)(hk >> 16), hj = 0xFFFFu - (uint32_t)(hk & 0xFFFFu);
   const uint64_t wl = work - hlen;
-  if (2 * wl > tmax) return false;
-  // T: the smallest power of two >= max(2 wl, 64)
-  const uint32_t need = umax32(2u * (uint32_t)wl, 64u);
+  if (wl > wmax) return false;
+  // T: the smallest power of two >= max(2 wl, 64), at most tmax (so the table
+  // is at most half full, or up to wmax / tmax in the largest one)
+  const uint32_t need = min(tmax, umax32(2u * (uint32_t)wl, 64u));
   const int logT = 32 - __clz(need - 1u);
   const uint32_t T = 1u << logT;
   const uint32_t mask = T - 1;
@@ -886,9 +894,9 @@ __global__ void __launch_bounds__(WinCfg<P>::THREADS, (Full<MODE>::value && WinC
     bool done = false;
     if (!Full<MODE>::value && threadIdx.x == 0) sh_seglen = seg_len_for(a.work[r], re - rb, WIN_SMAX);
     if ((MODE == MODE_TOTAL || MODE == MODE_EDGE) && a.hl_max && re > rb && re - rb <= (uint64_t)WIN_THREADS) {
-      done = count_hl<MODE, WIN_THREADS, WIN_WORDS>(a, rb, re, a.work[r], ctr,
-                                         (uint32_t)umin64(HL_TMAX, 2ull * a.hl_max), sm + WIN_WORDS, &sh_hmax,
-                                         wtot, acc);
+      done = count_hl<MODE, WIN_THREADS, WIN_WORDS>(a, rb, re, a.work[r], ctr, HL_TMAX,
+                                         (uint32_t)umin64(HL_TMAX / 4 * HL_FILL, a.hl_max), sm + WIN_WORDS,
+                                         &sh_hmax, wtot, acc);
       // otherwise, in EDGE mode, the longest list is walked as the heavy list of
       // the windows (it spares the read sweep of that list; in TOTAL mode the
       // extra barrier per window measured slower)
