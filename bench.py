@@ -42,7 +42,7 @@ CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.a
 # DRAM bytes (read + write) per call of each counting-kernel set, from one ncu
 # capture of the kernels' dram__bytes counters, valid only for the kernel
 # source they were taken with (its SHA-256 prefix).
-MEASURED_TRAFFIC = {"source_sha256": "767b6dda768af933",
+MEASURED_TRAFFIC = {"source_sha256": "8be147523665e5b3",
                     "bytes": {"win.edge": 17.10e9, "win.total": 5.92e9}}
 
 

@@ -386,7 +386,8 @@ struct Ctr {
 };
 
 // Count the wedge targets of one segment that fall in [lo, hi), starting at
-// cur; four 32-element loads in flight per warp.  Targets are ascending, so the
+// cur; one 32-element load first (most pieces end within it), then four in
+// flight per warp.  Targets are ascending, so the
 // in-window ones are a prefix.  On return cur is the first target >= hi (or
 // end) and nx that target's rank (INF_RANK at the end of the segment).
 // Raising a counter from c to c + 1 adds exactly c new pairs (C(c+1, 2) -
